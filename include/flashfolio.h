@@ -1,0 +1,164 @@
+/*
+ * flashfolio.h -- C ABI of the GB300 portfolio solver.
+ *
+ * The library solves the single-period portfolio model of Sec. 2.1 (Eqs. 1-3)
+ *
+ *     max_w  GMV alpha^T w - lambda1 GMV^2 w^T Sigma w
+ *            - lambda2 GMV s^T |w - w0| - lambda3 GMV q^T |w - w0|^d
+ *     s.t.   L <= A w <= U,   ||w||_1 <= 1,
+ *
+ * and the multi-period model of Sec. 2.2 (Eqs. 4-6), the same terms summed
+ * over t = 1..T with risk on (w_t - w_T), costs on (w_t - w_{t-1}), w_0 and w_T
+ * fixed and the constraints imposed for t = 1..T-1.  The risk matrix has the
+ * factor form Sigma = F Omega F^T + diag(D) of Sec. 3.2 (F is the paper's beta,
+ * Omega its Sigma_f).
+ *
+ * The paper gives no algorithm beyond "a first-order method that stops on a
+ * fixed-point residual, started at w0" (Sec. 4.1).  This library runs a
+ * restarted, reflected Halpern iteration of the Condat-Vu primal-dual
+ * splitting on
+ *     min f(x) + sum_t indicator(||x_t||_1 <= 1) + h_A(A x_t) + phi(Delta x + b)
+ * (f = return + risk, h_A = indicator of [L, U], phi = spread + impact cost
+ * on the trades) and stops on the relative KKT residual
+ *     max(r_primal, r_dual, r_gap) <= tol
+ * whose three parts are reported in ff_result.
+ *
+ * Conventions for every entry point:
+ *   - Pointers inside ff_problem are DEVICE pointers owned by the caller;
+ *     the library never frees or reallocates them and reads them only.
+ *   - ws is a caller-owned device workspace of at least ff_workspace_size()
+ *     bytes, 256-byte aligned.  Its contents are overwritten.
+ *   - All calls are asynchronous on the CUDA stream passed as `stream`
+ *     (a cudaStream_t; NULL = legacy default stream).  Device results are
+ *     valid once the stream reaches the point of the call.
+ *   - Return value: FF_OK or an FF_ERR_* code.  Argument errors are detected
+ *     on the host before anything is enqueued.  Nothing aborts, traps or
+ *     prints.  Per-instance solver outcomes are written to ff_result.status.
+ */
+#ifndef FLASHFOLIO_H
+#define FLASHFOLIO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes --------------------------------------------------- */
+#define FF_OK                  0
+#define FF_ERR_INVALID_ARG     1   /* a size, pointer, bound or option is invalid */
+#define FF_ERR_CUDA            2   /* a CUDA runtime call failed */
+#define FF_ERR_WORKSPACE       3   /* ws too small or misaligned */
+#define FF_ERR_UNSUPPORTED     4   /* shape exceeds what the kernels support */
+#define FF_ERR_DEVICE          5   /* device-side error flag (bounded wait expired) */
+
+/* ff_result.status (per instance) */
+#define FF_CONVERGED           0   /* relative KKT <= tol */
+#define FF_MAX_ITER            1   /* iteration limit reached */
+#define FF_TIME_LIMIT          2   /* device clock passed options.time_limit */
+#define FF_NUMERICAL           3   /* NaN/Inf met in the iteration */
+
+/* element types */
+#define FF_F64                 0
+#define FF_F32                 1
+
+/* precision modes of the solver */
+#define FF_PREC_F64            0   /* iterates, panels and reductions in FP64 */
+#define FF_PREC_F32            1   /* FP32 iterates and panels, FP64 reductions */
+#define FF_PREC_BF16           2   /* BF16 F and A panels, FP32 iterates, FP64 reductions */
+
+/* One problem instance in the paper's notation and units (Eqs. 1-6).
+ * Single period: T = 0; D, alpha, s, q hold n entries.
+ * Multi-period:  T >= 2; D, alpha, s, q hold T x n entries (row t-1 is period
+ *   t = 1..T; the row for t = T of alpha and D only enters a constant); wT
+ *   holds n entries.
+ * F is n x k row-major (asset-major), A is m x n row-major, Omega is k x k
+ * row-major (or its diagonal when omega_diag = 1).  L and U have m entries
+ * (+-INFINITY allowed, L <= U).  All arrays have element type `dtype`. */
+typedef struct ff_problem {
+    int32_t n, k, m;
+    int32_t T;
+    int32_t dtype;          /* FF_F64 or FF_F32 */
+    int32_t omega_diag;     /* 1: Omega points to k diagonal entries */
+    const void* F;
+    const void* Omega;
+    const void* D;
+    const void* alpha;
+    const void* s;
+    const void* q;
+    const void* w0;
+    const void* wT;         /* multi-period only, else NULL */
+    const void* A;          /* may be NULL when m = 0 */
+    const void* L;
+    const void* U;
+    double GMV, lambda1, lambda2, lambda3, d;   /* GMV > 0, lambda1 > 0, lambda2,3 >= 0, 1 < d <= 2 */
+} ff_problem;
+
+typedef struct ff_options {
+    double  tol;                /* relative KKT tolerance, default 1e-6 */
+    int64_t max_iter;           /* default 400000 */
+    double  time_limit;         /* seconds of device time, default 360 (Sec. 4.1) */
+    int32_t precision;          /* FF_PREC_*, default FF_PREC_F32 */
+    int32_t check_every;        /* iterations between KKT/restart checks, default 64 */
+    double  reflection;         /* Halpern reflection rho in [0, 1), default 0.9 */
+    double  restart_sufficient; /* default 0.2 */
+    double  restart_necessary;  /* default 0.8 */
+    double  step_fraction;      /* tau = step_fraction * 2 / L_f, default 0.5 */
+    int32_t cluster_size;       /* CTAs per instance: 0 = automatic, else 1, 2, 4, 8 or 16 */
+    int32_t max_teams;          /* batch: concurrent instance teams, 0 = as many as fit */
+} ff_options;
+
+/* Per-instance outcome, written to DEVICE memory by the solve calls. */
+typedef struct ff_result {
+    int32_t status;             /* FF_CONVERGED, FF_MAX_ITER, FF_TIME_LIMIT, FF_NUMERICAL */
+    int32_t restarts;
+    int64_t iterations;
+    double  rel_kkt;            /* max(r_primal, r_dual, r_gap) at the returned point */
+    double  r_primal, r_dual, r_gap;
+    double  primal_obj;         /* scaled minimisation objective P(x) = -(Eq. 1)/GMV (+ constant, multi) */
+    double  dual_obj;           /* the matching dual bound */
+    double  paper_obj;          /* Eq. 1 / Eq. 4 in the paper's units (maximised) */
+    double  fixed_point_res;    /* ||z - T(z)|| in the step-size metric at the last check */
+    double  seconds;            /* device time of this instance's solve */
+    double  lipschitz;          /* 2 lambda1 GMV lambda_max(Sigma) estimate used for the step */
+} ff_result;
+
+/* Fill *o with the defaults listed above. */
+void ff_default_options(ff_options* o);
+
+/* Bytes of device workspace for `count` instances (host only, no CUDA call).
+ * Returns 0 if an argument is invalid. */
+size_t ff_workspace_size(const ff_problem* probs, int count, const ff_options* o);
+
+/* Solve one single-period instance (p->T == 0).
+ *   result_dev : device pointer to one ff_result.
+ *   w_out      : device, n entries of p->dtype: the post-trade portfolio w.
+ *   yA_out     : device, m entries of p->dtype or NULL: exposure-row multipliers.
+ *   yD_out     : device, n entries of p->dtype or NULL: trade multipliers. */
+int ff_solve_single(const ff_problem* p, const ff_options* o, void* ws, size_t ws_bytes,
+                    ff_result* result_dev, void* w_out, void* yA_out, void* yD_out, void* stream);
+
+/* Solve one multi-period instance (p->T >= 2).
+ *   w_out  : device, (T-1) x n entries: w_1..w_{T-1}.
+ *   yA_out : device, (T-1) x m entries or NULL.   yD_out : device, T x n entries or NULL. */
+int ff_solve_multi(const ff_problem* p, const ff_options* o, void* ws, size_t ws_bytes,
+                   ff_result* result_dev, void* w_out, void* yA_out, void* yD_out, void* stream);
+
+/* Solve `count` independent instances (single- and multi-period mixed) in one
+ * persistent launch.  probs is a HOST array of count problems; w_out is a HOST
+ * array of count DEVICE pointers (layout as above); result_dev is a device
+ * array of count ff_result. */
+int ff_solve_batch(const ff_problem* probs, int count, const ff_options* o, void* ws, size_t ws_bytes,
+                   ff_result* result_dev, void* const* w_out, void* stream);
+
+/* Message for an FF_* return code (static storage). */
+const char* ff_status_string(int code);
+
+/* ABI version (major * 10000 + minor * 100 + patch). */
+int ff_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLASHFOLIO_H */

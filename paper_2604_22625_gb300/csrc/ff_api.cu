@@ -1,0 +1,388 @@
+// C ABI of the solver (declared in include/flashfolio.h): argument checks,
+// workspace carving, panel repacking and the launch of the team kernel.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ff_internal.cuh"
+
+namespace ff {
+namespace {
+
+constexpr size_t kAlign = 256;
+
+inline size_t a256(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+struct Sizes {
+    int n, k, m, P, R, np, multi;
+};
+
+inline Sizes sizes_of(const ff_problem& p) {
+    Sizes s;
+    s.n = p.n;
+    s.k = p.k;
+    s.m = p.m;
+    s.multi = p.T >= 2;
+    s.P = s.multi ? p.T - 1 : 1;
+    s.R = s.multi ? p.T : 1;
+    s.np = (p.n + 31) / 32 * 32;
+    return s;
+}
+
+inline size_t elem(int precision) { return precision == FF_PREC_F64 ? 8 : 4; }
+inline size_t panel_elem(int precision) {
+    return precision == FF_PREC_F64 ? 8 : (precision == FF_PREC_F32 ? 4 : 2);
+}
+
+// bytes of workspace of one instance (excluding the Inst table)
+size_t inst_bytes(const Sizes& s, int omega_diag, int precision) {
+    const size_t r = elem(precision), pe = panel_elem(precision);
+    size_t b = 0;
+    b += a256(2 * (size_t)s.k * s.np * pe);                 // F^T and F
+    b += a256(2 * (size_t)s.m * s.np * pe + 16);            // A and A^T
+    b += a256((size_t)(omega_diag ? s.k : s.k * s.k) * r);  // Omega
+    b += 2 * a256((size_t)s.P * s.np * r);                  // alpha, D
+    b += 4 * a256((size_t)s.np * r);                        // Dmax, w0, cen, alphaT
+    b += 2 * a256((size_t)s.R * s.np * r);                  // c1, c2
+    b += 2 * a256((size_t)s.m * r + 16);                    // L, U
+    b += 5 * a256((size_t)s.P * s.np * r);                  // x, x0, xb, xn, v
+    b += 4 * a256((size_t)s.R * s.np * r);                  // yD, yD0, yDb, yDn
+    b += 2 * a256((size_t)s.P * s.m * r + 16);              // yA0, ax0
+    b += a256((size_t)s.P * s.k * r);                       // u0
+    b += 2 * a256((size_t)s.np * r);                        // power-iteration vectors
+    return b;
+}
+
+size_t inst_struct_bytes(int precision) {
+    return precision == FF_PREC_F64 ? sizeof(Inst<double, double>)
+                                    : (precision == FF_PREC_F32 ? sizeof(Inst<float, float>)
+                                                                : sizeof(Inst<float, __nv_bfloat16>));
+}
+
+bool valid_problem(const ff_problem* p) {
+    if (!p) return false;
+    if (p->n < 1 || p->k < 1 || p->m < 0) return false;
+    if (!(p->T == 0 || p->T >= 2)) return false;
+    if (p->dtype != FF_F64 && p->dtype != FF_F32) return false;
+    if (!p->F || !p->Omega || !p->D || !p->alpha || !p->s || !p->q || !p->w0) return false;
+    if (p->m > 0 && (!p->A || !p->L || !p->U)) return false;
+    if (p->T >= 2 && !p->wT) return false;
+    if (!(p->GMV > 0) || !(p->lambda1 > 0) || !(p->lambda2 >= 0) || !(p->lambda3 >= 0)) return false;
+    if (!(p->d > 1.0 && p->d <= 2.0)) return false;
+    if (!isfinite(p->GMV) || !isfinite(p->lambda1) || !isfinite(p->lambda2) || !isfinite(p->lambda3))
+        return false;
+    return true;
+}
+
+bool supported(const Sizes& s, int omega_diag, int precision) {
+    if (s.P > 64) return false;              // per-period flags of the threshold search
+    if (s.k + s.m > 2 * kThreads) return false;
+    size_t smem = solver_smem_bytes(s.P, s.k, s.m, omega_diag, elem(precision));
+    return smem <= 227 * 1024 - 1024;   // static shared memory of the kernel needs the rest
+}
+
+void fill_defaults(ff_options* o) {
+    o->tol = 1e-6;
+    o->max_iter = 400000;
+    o->time_limit = 360.0;
+    o->precision = FF_PREC_F32;
+    o->check_every = 64;
+    o->reflection = 0.9;
+    o->restart_sufficient = 0.2;
+    o->restart_necessary = 0.8;
+    o->step_fraction = 0.5;
+    o->cluster_size = 0;
+    o->max_teams = 0;
+}
+
+bool valid_options(const ff_options& o) {
+    if (!(o.tol > 0) || o.max_iter < 1 || !(o.time_limit > 0)) return false;
+    if (o.precision < FF_PREC_F64 || o.precision > FF_PREC_BF16) return false;
+    if (o.check_every < 1 || !(o.reflection >= 0 && o.reflection < 1)) return false;
+    if (!(o.restart_sufficient > 0 && o.restart_sufficient < 1)) return false;
+    if (!(o.restart_necessary > 0 && o.restart_necessary < 1)) return false;
+    if (!(o.step_fraction > 0 && o.step_fraction < 1)) return false;
+    int g = o.cluster_size;
+    if (!(g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16)) return false;
+    if (o.max_teams < 0) return false;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// repack kernel: caller arrays (paper layout, FP32/FP64) -> workspace layout
+// ---------------------------------------------------------------------------
+template <class S> __device__ __forceinline__ S to_s(double v);
+template <> __device__ __forceinline__ double to_s<double>(double v) { return v; }
+template <> __device__ __forceinline__ float to_s<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ __nv_bfloat16 to_s<__nv_bfloat16>(double v) {
+    return __float2bfloat16_rn((float)v);
+}
+
+template <class In, class real, class S>
+__global__ void repack_kernel(ff_problem p, Inst<real, S> I, double lam2, double lam3) {
+    const In* F = (const In*)p.F;
+    const In* A = (const In*)p.A;
+    const In* Om = (const In*)p.Omega;
+    const In* D = (const In*)p.D;
+    const In* al = (const In*)p.alpha;
+    const In* s = (const In*)p.s;
+    const In* q = (const In*)p.q;
+    const In* w0 = (const In*)p.w0;
+    const In* wT = (const In*)p.wT;
+    const In* L = (const In*)p.L;
+    const In* U = (const In*)p.U;
+    const int n = I.n, k = I.k, m = I.m, P = I.P, R = I.R, np = I.np;
+    const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t nth = (size_t)gridDim.x * blockDim.x;
+    S* Ft = (S*)I.Ft;
+    S* Fam = Ft + (size_t)k * np;
+    S* At = (S*)I.At;
+    S* Aam = At + (size_t)m * np;
+    for (size_t e = tid; e < (size_t)np * k; e += nth) {
+        int i = (int)(e / k), j = (int)(e % k);
+        double v = (i < n) ? (double)F[(size_t)i * k + j] : 0.0;
+        Fam[e] = to_s<S>(v);
+        Ft[(size_t)j * np + i] = to_s<S>(v);
+    }
+    for (size_t e = tid; e < (size_t)np * m; e += nth) {
+        int i = (int)(e / m), j = (int)(e % m);
+        double v = (i < n) ? (double)A[(size_t)j * n + i] : 0.0;
+        Aam[e] = to_s<S>(v);
+        At[(size_t)j * np + i] = to_s<S>(v);
+    }
+    const int nOm = I.omega_diag ? k : k * k;
+    for (size_t e = tid; e < (size_t)nOm; e += nth) ((real*)I.Om)[e] = (real)Om[e];
+    for (size_t e = tid; e < (size_t)m; e += nth) {
+        ((real*)I.L)[e] = (real)L[e];
+        ((real*)I.U)[e] = (real)U[e];
+    }
+    for (size_t e = tid; e < (size_t)np; e += nth) {
+        int i = (int)e;
+        bool in = i < n;
+        double dmax = 0;
+        for (int pp = 0; pp < P; ++pp) {
+            double dv = in ? (double)D[(size_t)pp * n + i] : 0.0;
+            double av = in ? (double)al[(size_t)pp * n + i] : 0.0;
+            ((real*)I.Dp)[(size_t)pp * np + i] = (real)dv;
+            ((real*)I.alpha)[(size_t)pp * np + i] = (real)av;
+            dmax = fmax(dmax, dv);
+        }
+        ((real*)I.Dmax)[i] = (real)dmax;
+        for (int r = 0; r < R; ++r) {
+            ((real*)I.c1)[(size_t)r * np + i] = (real)(in ? lam2 * (double)s[(size_t)r * n + i] : 0.0);
+            ((real*)I.c2)[(size_t)r * np + i] = (real)(in ? lam3 * (double)q[(size_t)r * n + i] : 0.0);
+        }
+        ((real*)I.w0)[i] = (real)(in ? (double)w0[i] : 0.0);
+        ((real*)I.cen)[i] = (real)((in && I.multi) ? (double)wT[i] : 0.0);
+        if (I.multi) ((real*)I.alphaT)[i] = (real)(in ? (double)al[(size_t)P * n + i] : 0.0);
+    }
+}
+
+template <class real, class S>
+Inst<real, S> carve(const ff_problem& p, const Sizes& s, unsigned char*& cur, void* w_out, void* yA_out,
+                    void* yD_out, ff_result* res) {
+    Inst<real, S> I;
+    memset(&I, 0, sizeof(I));
+    I.n = s.n; I.k = s.k; I.m = s.m; I.P = s.P; I.R = s.R; I.multi = s.multi; I.np = s.np;
+    I.omega_diag = p.omega_diag ? 1 : 0;
+    auto take = [&](size_t bytes) { unsigned char* r = cur; cur += a256(bytes); return (void*)r; };
+    const size_t r = sizeof(real);
+    I.Ft = (const S*)take(2 * (size_t)s.k * s.np * sizeof(S));
+    I.At = (const S*)take(2 * (size_t)s.m * s.np * sizeof(S) + 16);
+    I.Om = (const real*)take((size_t)(I.omega_diag ? s.k : s.k * s.k) * r);
+    I.alpha = (const real*)take((size_t)s.P * s.np * r);
+    I.Dp = (const real*)take((size_t)s.P * s.np * r);
+    I.Dmax = (const real*)take((size_t)s.np * r);
+    I.w0 = (const real*)take((size_t)s.np * r);
+    I.cen = (const real*)take((size_t)s.np * r);
+    I.alphaT = (const real*)take((size_t)s.np * r);
+    I.c1 = (const real*)take((size_t)s.R * s.np * r);
+    I.c2 = (const real*)take((size_t)s.R * s.np * r);
+    I.L = (const real*)take((size_t)s.m * r + 16);
+    I.U = (const real*)take((size_t)s.m * r + 16);
+    I.x = (real*)take((size_t)s.P * s.np * r);
+    I.x0 = (real*)take((size_t)s.P * s.np * r);
+    I.xb = (real*)take((size_t)s.P * s.np * r);
+    I.xn = (real*)take((size_t)s.P * s.np * r);
+    I.v = (real*)take((size_t)s.P * s.np * r);
+    I.yD = (real*)take((size_t)s.R * s.np * r);
+    I.yD0 = (real*)take((size_t)s.R * s.np * r);
+    I.yDb = (real*)take((size_t)s.R * s.np * r);
+    I.yDn = (real*)take((size_t)s.R * s.np * r);
+    I.yA0 = (real*)take((size_t)s.P * s.m * r + 16);
+    I.ax0 = (real*)take((size_t)s.P * s.m * r + 16);
+    I.u0 = (real*)take((size_t)s.P * s.k * r);
+    I.pv1 = (real*)take((size_t)s.np * r);
+    I.pv2 = (real*)take((size_t)s.np * r);
+    I.kappa = (real)(p.lambda1 * p.GMV);
+    I.d = (real)p.d;
+    I.GMV = p.GMV;
+    I.w_out = w_out;
+    I.yA_out = yA_out;
+    I.yD_out = yD_out;
+    I.out_f64 = p.dtype == FF_F64;
+    I.res = res;
+    return I;
+}
+
+int auto_cluster(const Sizes& s, int count) {
+    if (count > 1) {
+        // batch: one CTA per instance keeps every SM busy with its own instance
+        return 1;
+    }
+    int g = 1;
+    while (g < 16 && (long long)s.n * s.P > (long long)g * 384) g *= 2;
+    return g;
+}
+
+template <class real, class S>
+int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_t ws_bytes, ff_result* res,
+        void* const* w_out, void* const* yA_out, void* const* yD_out, cudaStream_t stream) {
+    std::vector<Sizes> sz(count);
+    size_t need = a256((size_t)count * sizeof(Inst<real, S>));
+    size_t smem = 0;
+    long long maxwork = 0;
+    int maxn = 0;
+    for (int t = 0; t < count; ++t) {
+        sz[t] = sizes_of(probs[t]);
+        if (!supported(sz[t], probs[t].omega_diag, o.precision)) return FF_ERR_UNSUPPORTED;
+        need += inst_bytes(sz[t], probs[t].omega_diag, o.precision);
+        smem = std::max(smem, solver_smem_bytes(sz[t].P, sz[t].k, sz[t].m, probs[t].omega_diag, sizeof(real)));
+        maxn = std::max(maxn, sz[t].n * sz[t].P);
+        maxwork = std::max(maxwork, (long long)sz[t].n * sz[t].P * (sz[t].k + sz[t].m));
+    }
+    if (!ws || ((uintptr_t)ws % kAlign) != 0 || ws_bytes < need) return FF_ERR_WORKSPACE;
+    // LPT order: largest estimated work first, dealt round-robin to the teams
+    std::vector<int> order(count);
+    for (int t = 0; t < count; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        long long wa = (long long)sz[a].n * sz[a].P * (sz[a].k + sz[a].m);
+        long long wb = (long long)sz[b].n * sz[b].P * (sz[b].k + sz[b].m);
+        return wa > wb;
+    });
+    unsigned char* base = (unsigned char*)ws;
+    Inst<real, S>* table_dev = (Inst<real, S>*)base;
+    unsigned char* cur = base + a256((size_t)count * sizeof(Inst<real, S>));
+    std::vector<Inst<real, S>> table(count);
+    for (int slot = 0; slot < count; ++slot) {
+        int t = order[slot];
+        table[slot] = carve<real, S>(probs[t], sz[t], cur, w_out[t], yA_out ? yA_out[t] : nullptr,
+                                     yD_out ? yD_out[t] : nullptr, res + t);
+        const ff_problem& p = probs[t];
+        int blocks = (int)std::min<long long>(1024, ((long long)sz[t].np * std::max(sz[t].k, 1) + 255) / 256 + 1);
+        if (p.dtype == FF_F64)
+            repack_kernel<double, real, S><<<blocks, 256, 0, stream>>>(p, table[slot], p.lambda2, p.lambda3);
+        else
+            repack_kernel<float, real, S><<<blocks, 256, 0, stream>>>(p, table[slot], p.lambda2, p.lambda3);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return FF_ERR_CUDA;
+    }
+    cudaError_t e = cudaMemcpyAsync(table_dev, table.data(), (size_t)count * sizeof(Inst<real, S>),
+                                    cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return FF_ERR_CUDA;
+    int G = o.cluster_size > 0 ? o.cluster_size : auto_cluster(sz[order[0]], count);
+    int maxc = 0;
+    e = max_teams<real, S>(G, smem, &maxc);
+    if (e != cudaSuccess) return FF_ERR_CUDA;
+    if (maxc < 1) return FF_ERR_UNSUPPORTED;
+    int nteams = std::min(count, maxc);
+    if (o.max_teams > 0) nteams = std::min(nteams, o.max_teams);
+    Params prm;
+    prm.tol = o.tol;
+    prm.max_iter = o.max_iter;
+    prm.time_limit_ns = o.time_limit * 1e9;
+    prm.check_every = o.check_every;
+    prm.rho = o.reflection;
+    prm.beta_suff = o.restart_sufficient;
+    prm.beta_nec = o.restart_necessary;
+    prm.step_fraction = o.step_fraction;
+    prm.power_iters = 60;
+    e = launch_solver<real, S>(table_dev, count, prm, G, nteams, smem, stream);
+    if (e != cudaSuccess) return FF_ERR_CUDA;
+    (void)maxn;
+    (void)maxwork;
+    return FF_OK;
+}
+
+int dispatch(const ff_problem* probs, int count, const ff_options* o_in, void* ws, size_t ws_bytes,
+             ff_result* res, void* const* w_out, void* const* yA_out, void* const* yD_out, void* stream) {
+    if (count < 1 || !probs || !res || !w_out) return FF_ERR_INVALID_ARG;
+    ff_options o;
+    if (o_in) o = *o_in; else fill_defaults(&o);
+    if (!valid_options(o)) return FF_ERR_INVALID_ARG;
+    for (int t = 0; t < count; ++t) {
+        if (!valid_problem(&probs[t]) || !w_out[t]) return FF_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (o.precision) {
+        case FF_PREC_F64:
+            return run<double, double>(probs, count, o, ws, ws_bytes, res, w_out, yA_out, yD_out, st);
+        case FF_PREC_F32:
+            return run<float, float>(probs, count, o, ws, ws_bytes, res, w_out, yA_out, yD_out, st);
+        default:
+            return run<float, __nv_bfloat16>(probs, count, o, ws, ws_bytes, res, w_out, yA_out, yD_out, st);
+    }
+}
+
+}  // namespace
+}  // namespace ff
+
+extern "C" {
+
+void ff_default_options(ff_options* o) {
+    if (o) ff::fill_defaults(o);
+}
+
+size_t ff_workspace_size(const ff_problem* probs, int count, const ff_options* o_in) {
+    if (!probs || count < 1) return 0;
+    ff_options o;
+    if (o_in) o = *o_in; else ff::fill_defaults(&o);
+    if (!ff::valid_options(o)) return 0;
+    size_t need = ff::a256((size_t)count * ff::inst_struct_bytes(o.precision));
+    for (int t = 0; t < count; ++t) {
+        if (!ff::valid_problem(&probs[t])) return 0;
+        need += ff::inst_bytes(ff::sizes_of(probs[t]), probs[t].omega_diag, o.precision);
+    }
+    return need;
+}
+
+int ff_solve_single(const ff_problem* p, const ff_options* o, void* ws, size_t ws_bytes, ff_result* result_dev,
+                    void* w_out, void* yA_out, void* yD_out, void* stream) {
+    if (!p || p->T != 0) return FF_ERR_INVALID_ARG;
+    void* wo[1] = {w_out};
+    void* ya[1] = {yA_out};
+    void* yd[1] = {yD_out};
+    return ff::dispatch(p, 1, o, ws, ws_bytes, result_dev, wo, ya, yd, stream);
+}
+
+int ff_solve_multi(const ff_problem* p, const ff_options* o, void* ws, size_t ws_bytes, ff_result* result_dev,
+                   void* w_out, void* yA_out, void* yD_out, void* stream) {
+    if (!p || p->T < 2) return FF_ERR_INVALID_ARG;
+    void* wo[1] = {w_out};
+    void* ya[1] = {yA_out};
+    void* yd[1] = {yD_out};
+    return ff::dispatch(p, 1, o, ws, ws_bytes, result_dev, wo, ya, yd, stream);
+}
+
+int ff_solve_batch(const ff_problem* probs, int count, const ff_options* o, void* ws, size_t ws_bytes,
+                   ff_result* result_dev, void* const* w_out, void* stream) {
+    return ff::dispatch(probs, count, o, ws, ws_bytes, result_dev, w_out, nullptr, nullptr, stream);
+}
+
+const char* ff_status_string(int code) {
+    switch (code) {
+        case FF_OK: return "ok";
+        case FF_ERR_INVALID_ARG: return "invalid argument";
+        case FF_ERR_CUDA: return "CUDA runtime error";
+        case FF_ERR_WORKSPACE: return "workspace too small or misaligned";
+        case FF_ERR_UNSUPPORTED: return "problem shape not supported by the kernels";
+        case FF_ERR_DEVICE: return "device-side error flag set";
+        default: return "unknown status";
+    }
+}
+
+int ff_version(void) { return 100; }
+
+}  // extern "C"

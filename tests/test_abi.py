@@ -1,0 +1,63 @@
+"""The C-ABI library builds, loads and exports every entry point of include/flashfolio.h
+(no compute call: runs without a GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2604_22625_gb300 import _lib
+from paper_2604_22625_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return _lib.load()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "flashfolio.h")).read()
+    return sorted(set(re.findall(r"\b(ff_[a-z_]+)\s*\(", src)))
+
+
+def test_exports(lib):
+    names = _declared()
+    assert set(names) >= {"ff_solve_single", "ff_solve_multi", "ff_solve_batch", "ff_workspace_size",
+                          "ff_status_string", "ff_default_options", "ff_version"}
+    for nm in names:
+        assert hasattr(lib, nm), nm
+
+
+def test_struct_sizes_match_header(lib):
+    # ff_result layout mirrors the header (all 8-byte fields after two int32)
+    assert C.sizeof(_lib.ff_result) == 4 + 4 + 8 + 8 * 10
+    assert _lib.RESULT_DTYPE.itemsize == C.sizeof(_lib.ff_result)
+
+
+def test_host_only_calls(lib):
+    assert _lib.ff_version() >= 100
+    assert _lib.ff_status_string(_lib.FF_ERR_WORKSPACE).startswith("workspace")
+    o = _lib.default_options()
+    assert o.tol == 1e-6 and o.check_every == 64 and o.precision == _lib.FF_PREC_F32
+    # invalid problem -> workspace size 0, solve rejects before touching the GPU
+    p = _lib.ff_problem()
+    assert _lib.ff_workspace_size(C.byref(p), 1, o) == 0
+    rc = _lib.ff_solve_single(p, o, 0, 0, 0, 0)
+    assert rc == _lib.FF_ERR_INVALID_ARG
+
+
+def test_workspace_size_grows_with_n(lib):
+    o = _lib.default_options()
+
+    def ws(n, T=0):
+        p = _lib.ff_problem()
+        p.n, p.k, p.m, p.T, p.dtype, p.omega_diag = n, 10, 10, T, _lib.FF_F32, 1
+        for nm in ("F", "Omega", "D", "alpha", "s", "q", "w0", "A", "L", "U", "wT"):
+            setattr(p, nm, 1024)    # non-null placeholders: size query only
+        p.GMV, p.lambda1, p.lambda2, p.lambda3, p.d = 1e9, 1e-8, 1.0, 1.0, 1.5
+        return _lib.ff_workspace_size(C.byref(p), 1, o)
+
+    assert 0 < ws(100) < ws(1000) < ws(1000, T=5)
