@@ -101,12 +101,17 @@ typedef struct ff_options {
     double  time_limit;         /* seconds of device time, default 360 (Sec. 4.1) */
     int32_t precision;          /* FF_PREC_*, default FF_PREC_F32 */
     int32_t check_every;        /* iterations between KKT/restart checks, default 64 */
-    double  reflection;         /* Halpern reflection rho in [0, 1), default 0.9 */
+    double  reflection;         /* Halpern reflection rho, default 1/3; must satisfy
+                                   rho <= (2 beta - 1) / (2 beta) so that the reflected
+                                   operator stays nonexpansive */
     double  restart_sufficient; /* default 0.2 */
     double  restart_necessary;  /* default 0.8 */
-    double  step_fraction;      /* tau = step_fraction * 2 / L_f, default 0.5 */
+    double  step_fraction;      /* primal step tau = step_fraction * 2 / L_f, default 0.4 */
     int32_t cluster_size;       /* CTAs per instance: 0 = automatic, else 1, 2, 4, 8 or 16 */
     int32_t max_teams;          /* batch: concurrent instance teams, 0 = as many as fit */
+    double  beta;               /* dual steps sigma_i ||K_i||^2 sum to 1/tau - beta L_f, so the
+                                   smooth part is (beta)-cocoercive in the step metric; beta > 1/2,
+                                   default 0.75 */
 } ff_options;
 
 /* Per-instance outcome, written to DEVICE memory by the solve calls. */

@@ -51,7 +51,8 @@ class ff_options(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int64), ("time_limit", C.c_double),
                 ("precision", C.c_int32), ("check_every", C.c_int32), ("reflection", C.c_double),
                 ("restart_sufficient", C.c_double), ("restart_necessary", C.c_double),
-                ("step_fraction", C.c_double), ("cluster_size", C.c_int32), ("max_teams", C.c_int32)]
+                ("step_fraction", C.c_double), ("cluster_size", C.c_int32), ("max_teams", C.c_int32),
+                ("beta", C.c_double)]
 
 
 class ff_result(C.Structure):

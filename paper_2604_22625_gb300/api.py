@@ -42,11 +42,11 @@ def to_device(prob, dtype: torch.dtype = torch.float64, device: str = "cuda",
         if pinned_host is not None and nm in pinned_host:
             t[nm] = pinned_host[nm].to(device=device, non_blocking=True)
         else:
-            t[nm] = torch.as_tensor(np.ascontiguousarray(a), dtype=dtype).to(device)
+            t[nm] = torch.as_tensor(np.array(a, dtype=np.float64, copy=True), dtype=dtype).to(device)
     omega_diag = 0
     Om = np.asarray(prob.Omega)
     if Om.ndim == 2 and np.count_nonzero(Om - np.diag(np.diag(Om))) == 0:
-        t["Omega"] = torch.as_tensor(np.ascontiguousarray(np.diag(Om)), dtype=dtype).to(device)
+        t["Omega"] = torch.as_tensor(np.array(np.diag(Om), dtype=np.float64, copy=True), dtype=dtype).to(device)
         omega_diag = 1
     n, k = prob.F.shape
     m = prob.A.shape[0]
@@ -116,7 +116,7 @@ def solve(prob, precision: str = "f32", device: str = "cuda", return_duals: bool
     wn = w.cpu().numpy().astype(np.float64)
     if int(prob.T) >= 2:
         wn = wn.reshape(dp.P, dp.n)
-    return Solution(wn, yA.cpu().numpy().astype(np.float64).reshape(dp.P, dp.m) if yA is not None else None,
+    return Solution(wn, yA.cpu().numpy().astype(np.float64)[:dp.P * dp.m].reshape(dp.P, dp.m) if yA is not None else None,
                     yD.cpu().numpy().astype(np.float64).reshape(dp.R, dp.n) if yD is not None else None,
                     _info(rec))
 

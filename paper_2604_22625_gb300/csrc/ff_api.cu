@@ -31,14 +31,14 @@ inline Sizes sizes_of(const ff_problem& p) {
     return s;
 }
 
-inline size_t elem(int precision) { return precision == FF_PREC_F64 ? 8 : 4; }
+inline size_t matvec_elem(int precision) { return precision == FF_PREC_F64 ? 8 : 4; }
 inline size_t panel_elem(int precision) {
     return precision == FF_PREC_F64 ? 8 : (precision == FF_PREC_F32 ? 4 : 2);
 }
 
-// bytes of workspace of one instance (excluding the Inst table)
+// bytes of workspace of one instance (excluding the Inst table); state is FP64
 size_t inst_bytes(const Sizes& s, int omega_diag, int precision) {
-    const size_t r = elem(precision), pe = panel_elem(precision);
+    const size_t r = 8, pe = panel_elem(precision);
     size_t b = 0;
     b += a256(2 * (size_t)s.k * s.np * pe);                 // F^T and F
     b += a256(2 * (size_t)s.m * s.np * pe + 16);            // A and A^T
@@ -49,8 +49,7 @@ size_t inst_bytes(const Sizes& s, int omega_diag, int precision) {
     b += 2 * a256((size_t)s.m * r + 16);                    // L, U
     b += 5 * a256((size_t)s.P * s.np * r);                  // x, x0, xb, xn, v
     b += 4 * a256((size_t)s.R * s.np * r);                  // yD, yD0, yDb, yDn
-    b += 2 * a256((size_t)s.P * s.m * r + 16);              // yA0, ax0
-    b += a256((size_t)s.P * s.k * r);                       // u0
+    b += a256((size_t)s.P * s.m * r + 16);                  // yA0
     b += 2 * a256((size_t)s.np * r);                        // power-iteration vectors
     return b;
 }
@@ -79,7 +78,7 @@ bool valid_problem(const ff_problem* p) {
 bool supported(const Sizes& s, int omega_diag, int precision) {
     if (s.P > 64) return false;              // per-period flags of the threshold search
     if (s.k + s.m > 2 * kThreads) return false;
-    size_t smem = solver_smem_bytes(s.P, s.k, s.m, omega_diag, elem(precision));
+    size_t smem = solver_smem_bytes(s.P, s.k, s.m, omega_diag, matvec_elem(precision));
     return smem <= 227 * 1024 - 1024;   // static shared memory of the kernel needs the rest
 }
 
@@ -89,10 +88,11 @@ void fill_defaults(ff_options* o) {
     o->time_limit = 360.0;
     o->precision = FF_PREC_F32;
     o->check_every = 64;
-    o->reflection = 0.9;
+    o->reflection = 1.0 / 3.0;
     o->restart_sufficient = 0.2;
     o->restart_necessary = 0.8;
-    o->step_fraction = 0.5;
+    o->step_fraction = 0.4;
+    o->beta = 0.75;
     o->cluster_size = 0;
     o->max_teams = 0;
 }
@@ -104,6 +104,9 @@ bool valid_options(const ff_options& o) {
     if (!(o.restart_sufficient > 0 && o.restart_sufficient < 1)) return false;
     if (!(o.restart_necessary > 0 && o.restart_necessary < 1)) return false;
     if (!(o.step_fraction > 0 && o.step_fraction < 1)) return false;
+    // the dual steps need 1/tau - beta L_f > 0, i.e. 2 step_fraction beta < 1
+    if (!(o.beta > 0.5) || !(2.0 * o.step_fraction * o.beta < 1.0)) return false;
+    if (o.reflection > (2.0 * o.beta - 1.0) / (2.0 * o.beta) + 1e-12) return false;
     int g = o.cluster_size;
     if (!(g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16)) return false;
     if (o.max_teams < 0) return false;
@@ -120,8 +123,8 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_s<__nv_bfloat16>(double 
     return __float2bfloat16_rn((float)v);
 }
 
-template <class In, class real, class S>
-__global__ void repack_kernel(ff_problem p, Inst<real, S> I, double lam2, double lam3) {
+template <class In, class M, class S>
+__global__ void repack_kernel(ff_problem p, Inst<M, S> I, double lam2, double lam3) {
     const In* F = (const In*)p.F;
     const In* A = (const In*)p.A;
     const In* Om = (const In*)p.Omega;
@@ -153,10 +156,10 @@ __global__ void repack_kernel(ff_problem p, Inst<real, S> I, double lam2, double
         At[(size_t)j * np + i] = to_s<S>(v);
     }
     const int nOm = I.omega_diag ? k : k * k;
-    for (size_t e = tid; e < (size_t)nOm; e += nth) ((real*)I.Om)[e] = (real)Om[e];
+    for (size_t e = tid; e < (size_t)nOm; e += nth) ((double*)I.Om)[e] = (double)Om[e];
     for (size_t e = tid; e < (size_t)m; e += nth) {
-        ((real*)I.L)[e] = (real)L[e];
-        ((real*)I.U)[e] = (real)U[e];
+        ((double*)I.L)[e] = (double)L[e];
+        ((double*)I.U)[e] = (double)U[e];
     }
     for (size_t e = tid; e < (size_t)np; e += nth) {
         int i = (int)e;
@@ -165,59 +168,57 @@ __global__ void repack_kernel(ff_problem p, Inst<real, S> I, double lam2, double
         for (int pp = 0; pp < P; ++pp) {
             double dv = in ? (double)D[(size_t)pp * n + i] : 0.0;
             double av = in ? (double)al[(size_t)pp * n + i] : 0.0;
-            ((real*)I.Dp)[(size_t)pp * np + i] = (real)dv;
-            ((real*)I.alpha)[(size_t)pp * np + i] = (real)av;
+            ((double*)I.Dp)[(size_t)pp * np + i] = (double)dv;
+            ((double*)I.alpha)[(size_t)pp * np + i] = (double)av;
             dmax = fmax(dmax, dv);
         }
-        ((real*)I.Dmax)[i] = (real)dmax;
+        ((double*)I.Dmax)[i] = (double)dmax;
         for (int r = 0; r < R; ++r) {
-            ((real*)I.c1)[(size_t)r * np + i] = (real)(in ? lam2 * (double)s[(size_t)r * n + i] : 0.0);
-            ((real*)I.c2)[(size_t)r * np + i] = (real)(in ? lam3 * (double)q[(size_t)r * n + i] : 0.0);
+            ((double*)I.c1)[(size_t)r * np + i] = (double)(in ? lam2 * (double)s[(size_t)r * n + i] : 0.0);
+            ((double*)I.c2)[(size_t)r * np + i] = (double)(in ? lam3 * (double)q[(size_t)r * n + i] : 0.0);
         }
-        ((real*)I.w0)[i] = (real)(in ? (double)w0[i] : 0.0);
-        ((real*)I.cen)[i] = (real)((in && I.multi) ? (double)wT[i] : 0.0);
-        if (I.multi) ((real*)I.alphaT)[i] = (real)(in ? (double)al[(size_t)P * n + i] : 0.0);
+        ((double*)I.w0)[i] = (double)(in ? (double)w0[i] : 0.0);
+        ((double*)I.cen)[i] = (double)((in && I.multi) ? (double)wT[i] : 0.0);
+        if (I.multi) ((double*)I.alphaT)[i] = (double)(in ? (double)al[(size_t)P * n + i] : 0.0);
     }
 }
 
-template <class real, class S>
-Inst<real, S> carve(const ff_problem& p, const Sizes& s, unsigned char*& cur, void* w_out, void* yA_out,
-                    void* yD_out, ff_result* res) {
-    Inst<real, S> I;
+template <class M, class S>
+Inst<M, S> carve(const ff_problem& p, const Sizes& s, unsigned char*& cur, void* w_out, void* yA_out,
+                 void* yD_out, ff_result* res) {
+    Inst<M, S> I;
     memset(&I, 0, sizeof(I));
     I.n = s.n; I.k = s.k; I.m = s.m; I.P = s.P; I.R = s.R; I.multi = s.multi; I.np = s.np;
     I.omega_diag = p.omega_diag ? 1 : 0;
     auto take = [&](size_t bytes) { unsigned char* r = cur; cur += a256(bytes); return (void*)r; };
-    const size_t r = sizeof(real);
+    const size_t r = sizeof(double);
     I.Ft = (const S*)take(2 * (size_t)s.k * s.np * sizeof(S));
     I.At = (const S*)take(2 * (size_t)s.m * s.np * sizeof(S) + 16);
-    I.Om = (const real*)take((size_t)(I.omega_diag ? s.k : s.k * s.k) * r);
-    I.alpha = (const real*)take((size_t)s.P * s.np * r);
-    I.Dp = (const real*)take((size_t)s.P * s.np * r);
-    I.Dmax = (const real*)take((size_t)s.np * r);
-    I.w0 = (const real*)take((size_t)s.np * r);
-    I.cen = (const real*)take((size_t)s.np * r);
-    I.alphaT = (const real*)take((size_t)s.np * r);
-    I.c1 = (const real*)take((size_t)s.R * s.np * r);
-    I.c2 = (const real*)take((size_t)s.R * s.np * r);
-    I.L = (const real*)take((size_t)s.m * r + 16);
-    I.U = (const real*)take((size_t)s.m * r + 16);
-    I.x = (real*)take((size_t)s.P * s.np * r);
-    I.x0 = (real*)take((size_t)s.P * s.np * r);
-    I.xb = (real*)take((size_t)s.P * s.np * r);
-    I.xn = (real*)take((size_t)s.P * s.np * r);
-    I.v = (real*)take((size_t)s.P * s.np * r);
-    I.yD = (real*)take((size_t)s.R * s.np * r);
-    I.yD0 = (real*)take((size_t)s.R * s.np * r);
-    I.yDb = (real*)take((size_t)s.R * s.np * r);
-    I.yDn = (real*)take((size_t)s.R * s.np * r);
-    I.yA0 = (real*)take((size_t)s.P * s.m * r + 16);
-    I.ax0 = (real*)take((size_t)s.P * s.m * r + 16);
-    I.u0 = (real*)take((size_t)s.P * s.k * r);
-    I.pv1 = (real*)take((size_t)s.np * r);
-    I.pv2 = (real*)take((size_t)s.np * r);
-    I.kappa = (real)(p.lambda1 * p.GMV);
-    I.d = (real)p.d;
+    I.Om = (const double*)take((size_t)(I.omega_diag ? s.k : s.k * s.k) * r);
+    I.alpha = (const double*)take((size_t)s.P * s.np * r);
+    I.Dp = (const double*)take((size_t)s.P * s.np * r);
+    I.Dmax = (const double*)take((size_t)s.np * r);
+    I.w0 = (const double*)take((size_t)s.np * r);
+    I.cen = (const double*)take((size_t)s.np * r);
+    I.alphaT = (const double*)take((size_t)s.np * r);
+    I.c1 = (const double*)take((size_t)s.R * s.np * r);
+    I.c2 = (const double*)take((size_t)s.R * s.np * r);
+    I.L = (const double*)take((size_t)s.m * r + 16);
+    I.U = (const double*)take((size_t)s.m * r + 16);
+    I.x = (double*)take((size_t)s.P * s.np * r);
+    I.x0 = (double*)take((size_t)s.P * s.np * r);
+    I.xb = (double*)take((size_t)s.P * s.np * r);
+    I.xn = (double*)take((size_t)s.P * s.np * r);
+    I.v = (double*)take((size_t)s.P * s.np * r);
+    I.yD = (double*)take((size_t)s.R * s.np * r);
+    I.yD0 = (double*)take((size_t)s.R * s.np * r);
+    I.yDb = (double*)take((size_t)s.R * s.np * r);
+    I.yDn = (double*)take((size_t)s.R * s.np * r);
+    I.yA0 = (double*)take((size_t)s.P * s.m * r + 16);
+    I.pv1 = (double*)take((size_t)s.np * r);
+    I.pv2 = (double*)take((size_t)s.np * r);
+    I.kappa = p.lambda1 * p.GMV;
+    I.d = p.d;
     I.GMV = p.GMV;
     I.w_out = w_out;
     I.yA_out = yA_out;
@@ -237,11 +238,11 @@ int auto_cluster(const Sizes& s, int count) {
     return g;
 }
 
-template <class real, class S>
+template <class M, class S>
 int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_t ws_bytes, ff_result* res,
         void* const* w_out, void* const* yA_out, void* const* yD_out, cudaStream_t stream) {
     std::vector<Sizes> sz(count);
-    size_t need = a256((size_t)count * sizeof(Inst<real, S>));
+    size_t need = a256((size_t)count * sizeof(Inst<M, S>));
     size_t smem = 0;
     long long maxwork = 0;
     int maxn = 0;
@@ -249,7 +250,7 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
         sz[t] = sizes_of(probs[t]);
         if (!supported(sz[t], probs[t].omega_diag, o.precision)) return FF_ERR_UNSUPPORTED;
         need += inst_bytes(sz[t], probs[t].omega_diag, o.precision);
-        smem = std::max(smem, solver_smem_bytes(sz[t].P, sz[t].k, sz[t].m, probs[t].omega_diag, sizeof(real)));
+        smem = std::max(smem, solver_smem_bytes(sz[t].P, sz[t].k, sz[t].m, probs[t].omega_diag, sizeof(double)));
         maxn = std::max(maxn, sz[t].n * sz[t].P);
         maxwork = std::max(maxwork, (long long)sz[t].n * sz[t].P * (sz[t].k + sz[t].m));
     }
@@ -263,28 +264,28 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
         return wa > wb;
     });
     unsigned char* base = (unsigned char*)ws;
-    Inst<real, S>* table_dev = (Inst<real, S>*)base;
-    unsigned char* cur = base + a256((size_t)count * sizeof(Inst<real, S>));
-    std::vector<Inst<real, S>> table(count);
+    Inst<M, S>* table_dev = (Inst<M, S>*)base;
+    unsigned char* cur = base + a256((size_t)count * sizeof(Inst<M, S>));
+    std::vector<Inst<M, S>> table(count);
     for (int slot = 0; slot < count; ++slot) {
         int t = order[slot];
-        table[slot] = carve<real, S>(probs[t], sz[t], cur, w_out[t], yA_out ? yA_out[t] : nullptr,
+        table[slot] = carve<M, S>(probs[t], sz[t], cur, w_out[t], yA_out ? yA_out[t] : nullptr,
                                      yD_out ? yD_out[t] : nullptr, res + t);
         const ff_problem& p = probs[t];
         int blocks = (int)std::min<long long>(1024, ((long long)sz[t].np * std::max(sz[t].k, 1) + 255) / 256 + 1);
         if (p.dtype == FF_F64)
-            repack_kernel<double, real, S><<<blocks, 256, 0, stream>>>(p, table[slot], p.lambda2, p.lambda3);
+            repack_kernel<double, M, S><<<blocks, 256, 0, stream>>>(p, table[slot], p.lambda2, p.lambda3);
         else
-            repack_kernel<float, real, S><<<blocks, 256, 0, stream>>>(p, table[slot], p.lambda2, p.lambda3);
+            repack_kernel<float, M, S><<<blocks, 256, 0, stream>>>(p, table[slot], p.lambda2, p.lambda3);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return FF_ERR_CUDA;
     }
-    cudaError_t e = cudaMemcpyAsync(table_dev, table.data(), (size_t)count * sizeof(Inst<real, S>),
+    cudaError_t e = cudaMemcpyAsync(table_dev, table.data(), (size_t)count * sizeof(Inst<M, S>),
                                     cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return FF_ERR_CUDA;
     int G = o.cluster_size > 0 ? o.cluster_size : auto_cluster(sz[order[0]], count);
     int maxc = 0;
-    e = max_teams<real, S>(G, smem, &maxc);
+    e = max_teams<M, S>(G, smem, &maxc);
     if (e != cudaSuccess) return FF_ERR_CUDA;
     if (maxc < 1) return FF_ERR_UNSUPPORTED;
     int nteams = std::min(count, maxc);
@@ -298,8 +299,9 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
     prm.beta_suff = o.restart_sufficient;
     prm.beta_nec = o.restart_necessary;
     prm.step_fraction = o.step_fraction;
+    prm.beta = o.beta;
     prm.power_iters = 60;
-    e = launch_solver<real, S>(table_dev, count, prm, G, nteams, smem, stream);
+    e = launch_solver<M, S>(table_dev, count, prm, G, nteams, smem, stream);
     if (e != cudaSuccess) return FF_ERR_CUDA;
     (void)maxn;
     (void)maxwork;

@@ -12,35 +12,38 @@ namespace ff {
 constexpr int kThreads = 256;          // threads per CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kPC = 8;                 // periods processed together in a matvec pass
+constexpr int kCH = 64;                // assets staged per step of the reduce pass
 constexpr int kCand = 8;               // threshold candidates per period and search round
 constexpr int kMaxRounds = 16;         // threshold search rounds per projection
 constexpr int kMaxCluster = 16;
 
 // One instance as the solver kernel sees it (device memory).  All per-asset
-// arrays have row stride np (n rounded up to a multiple of 32).
-template <class real, class S>
+// arrays have row stride np (n rounded up to a multiple of 32).  Panels are
+// stored as S (double, float or bfloat16) and multiplied in M (double or
+// float); the iterate state and every elementwise update are FP64.
+template <class M, class S>
 struct Inst {
     int n, k, m, P, R, multi, np, omega_diag;
-    const S* Ft;        // k x np   factor loadings, factor-major (F^T)
-    const S* At;        // m x np   exposure rows
-    const real* Om;     // k x k, or k diagonal entries
-    const real* alpha;  // P x np
-    const real* Dp;     // P x np
-    const real* Dmax;   // np       max over periods of D (for the Lipschitz bound)
-    const real* c1;     // R x np   lambda2 * s
-    const real* c2;     // R x np   lambda3 * q
-    const real* w0;     // np
-    const real* cen;    // np       risk centre: w_T (multi) or 0 (single)
-    const real* alphaT; // np       alpha at t = T (multi) or nullptr
-    const real* L;      // m
-    const real* U;      // m
-    real kappa, d;
+    const S* Ft;          // k x np factor-major F^T, followed by np x k asset-major F
+    const S* At;          // m x np exposure rows, followed by np x m asset-major A^T
+    const double* Om;     // k x k, or k diagonal entries
+    const double* alpha;  // P x np
+    const double* Dp;     // P x np
+    const double* Dmax;   // np       max over periods of D (for the Lipschitz bound)
+    const double* c1;     // R x np   lambda2 * s
+    const double* c2;     // R x np   lambda3 * q
+    const double* w0;     // np
+    const double* cen;    // np       risk centre: w_T (multi) or 0 (single)
+    const double* alphaT; // np       alpha at t = T (multi) or unused
+    const double* L;      // m
+    const double* U;      // m
+    double kappa, d;
     double GMV;
     // iterate storage (workspace)
-    real *x, *x0, *xb, *xn, *v;        // P x np
-    real *yD, *yD0, *yDb, *yDn;        // R x np
-    real *yA0, *u0, *ax0;              // P x m, P x k, P x m (anchors of the replicated vectors)
-    real *pv1, *pv2;                   // np power-iteration vectors
+    double *x, *x0, *xb, *xn, *v;      // P x np
+    double *yD, *yD0, *yDb, *yDn;      // R x np
+    double* yA0;                       // P x m anchor of the replicated y_A
+    double *pv1, *pv2;                 // np power-iteration vectors
     // outputs
     void* w_out;        // P x n   (out dtype)
     void* yA_out;       // P x m   or nullptr
@@ -57,19 +60,20 @@ struct Params {
     double rho;
     double beta_suff, beta_nec;
     double step_fraction;
+    double beta;
     int power_iters;
 };
 
 // Shared-memory bytes the solver kernel needs for these sizes.
-size_t solver_smem_bytes(int P, int k, int m, int omega_diag, size_t real_size);
+size_t solver_smem_bytes(int P, int k, int m, int omega_diag, size_t matvec_size);
 
 // Launch the team kernel over `count` instances (insts is a device array).
 // G = CTAs per instance (cluster size), nteams = concurrent teams.
-template <class real, class S>
-cudaError_t launch_solver(const Inst<real, S>* insts, int count, const Params& prm, int G, int nteams,
+template <class M, class S>
+cudaError_t launch_solver(const Inst<M, S>* insts, int count, const Params& prm, int G, int nteams,
                           size_t smem, cudaStream_t stream);
 
-template <class real, class S>
+template <class M, class S>
 cudaError_t max_teams(int G, size_t smem, int* out);
 
 }  // namespace ff

@@ -42,6 +42,7 @@ def test_host_only_calls(lib):
     assert _lib.ff_status_string(_lib.FF_ERR_WORKSPACE).startswith("workspace")
     o = _lib.default_options()
     assert o.tol == 1e-6 and o.check_every == 64 and o.precision == _lib.FF_PREC_F32
+    assert abs(o.reflection - 1 / 3) < 1e-15 and o.beta == 0.75 and o.step_fraction == 0.4
     # invalid problem -> workspace size 0, solve rejects before touching the GPU
     p = _lib.ff_problem()
     assert _lib.ff_workspace_size(C.byref(p), 1, o) == 0
