@@ -127,6 +127,10 @@ typedef struct ff_result {
     double  fixed_point_res;    /* ||z - T(z)|| in the step-size metric at the last check */
     double  seconds;            /* device time of this instance's solve */
     double  lipschitz;          /* 2 lambda1 GMV lambda_max(Sigma) estimate used for the step */
+    int64_t threshold_rounds;   /* rounds of the l1-threshold search over the whole solve */
+    double  phase_seconds[6];   /* device time by phase (rank 0 of the team): setup,
+                                   expand pass, l1 thresholds, elementwise prox,
+                                   reduce pass + team sums, KKT checks */
 } ff_result;
 
 /* Fill *o with the defaults listed above. */

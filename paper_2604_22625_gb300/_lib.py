@@ -60,10 +60,12 @@ class ff_result(C.Structure):
                 ("rel_kkt", C.c_double), ("r_primal", C.c_double), ("r_dual", C.c_double),
                 ("r_gap", C.c_double), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("paper_obj", C.c_double), ("fixed_point_res", C.c_double), ("seconds", C.c_double),
-                ("lipschitz", C.c_double)]
+                ("lipschitz", C.c_double), ("threshold_rounds", C.c_int64),
+                ("phase_seconds", C.c_double * 6)]
 
 
 RESULT_DTYPE = np.dtype([(name, {C.c_int32: np.int32, C.c_int64: np.int64, C.c_double: np.float64}[ct])
+                         if ct in (C.c_int32, C.c_int64, C.c_double) else (name, np.float64, (6,))
                          for name, ct in ff_result._fields_], align=True)
 assert RESULT_DTYPE.itemsize == C.sizeof(ff_result)
 

@@ -79,7 +79,7 @@ class Solution:
 
 
 def _info(rec) -> dict:
-    d = {name: rec[name].item() for name in L.RESULT_DTYPE.names}
+    d = {name: (rec[name].tolist() if rec[name].ndim else rec[name].item()) for name in L.RESULT_DTYPE.names}
     d["status_name"] = L.STATUS_NAMES.get(d["status"], str(d["status"]))
     return d
 

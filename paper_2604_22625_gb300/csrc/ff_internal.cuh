@@ -12,7 +12,6 @@ namespace ff {
 constexpr int kThreads = 256;          // threads per CTA
 constexpr int kWarps = kThreads / 32;
 constexpr int kPC = 8;                 // periods processed together in a matvec pass
-constexpr int kCH = 64;                // assets staged per step of the reduce pass
 constexpr int kCand = 8;               // threshold candidates per period and search round
 constexpr int kMaxRounds = 16;         // threshold search rounds per projection
 constexpr int kMaxCluster = 16;

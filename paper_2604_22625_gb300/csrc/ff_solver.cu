@@ -43,13 +43,13 @@ struct Layout {
     size_t vpart, vout;        // double, vlen each (one chunk of kPC periods)
     size_t spart, sout;        // double, slen each
     size_t wred;               // double, kWarps * 32
-    size_t stage;              // M, 4 * kPC * kCH
+    size_t stage;              // M, 2048 (4 vectors x PCT periods x 512/PCT assets)
     size_t yA, yAb, ax;        // double, P*m each
     size_t u, ub;              // double, P*k each
     size_t om;                 // M, P*k
     size_t yAm;                // M, P*m
     size_t Om;                 // double, k*k or k
-    size_t cand, thprev, theta;
+    size_t cand, thprev, theta, thq;
     size_t lb, ubd;            // double, m each
     size_t total;
     int vlen, slen;
@@ -60,6 +60,8 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 __host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_diag, size_t ms) {
     Layout L;
     L.vlen = kPC * (2 * m + 2 * k);
+    const int slots = (kWarps * P * kCand + 1) / 2;   // 4-byte threshold slots in 8-byte units
+    if (L.vlen < slots) L.vlen = slots;
     int s1 = P * kCand * 2, s2 = P + 48;
     L.slen = s1 > s2 ? s1 : s2;
     size_t o = 0;
@@ -69,18 +71,20 @@ __host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_dia
     L.spart = take((size_t)L.slen * 8);
     L.sout = take((size_t)L.slen * 8);
     L.wred = take((size_t)kWarps * 32 * 8);
-    L.stage = take((size_t)4 * kPC * kCH * ms);
+    L.stage = take((size_t)2048 * ms);              // 4 vectors x PCT periods x 512/PCT assets
     L.yA = take((size_t)P * m * 8);
-    L.yAb = take((size_t)P * m * 8);
+    L.yAb = take((size_t)((P + kPC - 1) / kPC * kPC) * m * 8);
     L.ax = take((size_t)P * m * 8);
+    const int Pr = (P + kPC - 1) / kPC * kPC;        // whole chunks for the expand pass weights
     L.u = take((size_t)P * k * 8);
-    L.ub = take((size_t)P * k * 8);
-    L.om = take((size_t)P * k * ms);
-    L.yAm = take((size_t)P * m * ms);
+    L.ub = take((size_t)Pr * k * 8);
+    L.om = take((size_t)Pr * k * ms);
+    L.yAm = take((size_t)Pr * m * ms);
     L.Om = take((size_t)(omega_diag ? k : k * k) * 8);
     L.cand = take((size_t)P * kCand * 8);
     L.thprev = take((size_t)P * 8);
     L.theta = take((size_t)P * 8);
+    L.thq = take((size_t)P * 8);
     L.lb = take((size_t)m * 8);
     L.ubd = take((size_t)m * 8);
     L.total = o;
@@ -149,6 +153,39 @@ __device__ __forceinline__ double cost_conj(double y, double c1, double c2, doub
     return a * r * (1.0 - 1.0 / d);
 }
 
+// Dual update of one trade row (Moreau identity for h_D(v) = phi(v + b)):
+//   t = p / sigma + b,  z = prox_{phi / sigma}(t),  y = sigma (t - z).
+// On the live branch (|t| > c1 / sigma) y = phi'(z) = sign(t) (c1 + d c2 |z|^(d-1)),
+// evaluated in M without the cancellation of p - sigma (z - b); in the dead zone
+// y = sigma t = p + sigma b exactly.  Returns true on the live branch.
+template <class M>
+__device__ __forceinline__ bool trade_multiplier(double t, double inv_sigma, double c1d, double c2d, double d,
+                                                 M& y_live) {
+    const M c1 = (M)c1d, c2 = (M)c2d;
+    const M g = (M)inv_sigma;
+    const M tm = (M)t;
+    const M a = fabs(tm) - g * c1;
+    if (!(a > (M)0)) return false;
+    M deriv;
+    const M gc = g * c2;
+    if (gc <= (M)0) {
+        deriv = c1;
+    } else if (d == 1.5) {
+        // z = rho^2 with rho^2 + beta rho - a = 0, beta = 1.5 g c2: phi'(z) = c1 + 1.5 c2 rho
+        const M beta = (M)1.5 * gc;
+        const M rho = (M)2 * a / (beta + sqrt(beta * beta + (M)4 * a));
+        deriv = c1 + (M)1.5 * c2 * rho;
+    } else if (d == 2.0) {
+        deriv = c1 + (M)2 * c2 * (a / ((M)1 + (M)2 * gc));
+    } else {
+        // general exponent: FP64 safeguarded Newton for |z|, derivative in M
+        const M r = (M)fabs(prox_cost(t, inv_sigma, c1d, c2d, d));
+        deriv = c1 + (M)d * c2 * (M)pow((double)r, d - 1.0);
+    }
+    y_live = tm < 0 ? -deriv : deriv;
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // per-CTA context
 // ---------------------------------------------------------------------------
@@ -163,29 +200,33 @@ struct Ctx {
     M* stage;
     double *yA, *yAb, *ax, *u, *ub, *Om, *lb, *ubd;
     M *om, *yAm;
-    double *cand, *thprev, *theta;
+    double *cand, *thprev, *theta, *thq;
 };
 
 // Sum (or max) of part[0..K) over the team; result in out[0..K) of every CTA.
+// The G remote loads of an entry are issued together and added in rank order,
+// so every CTA receives bit-identical totals.
 template <bool MAX>
 __device__ void team_reduce(cg::cluster_group& cl, double* part, double* out, int K, int G, int g) {
     cl.sync();
-    int per = (K + G - 1) / G;
-    int lo = g * per;
-    int hi = min(K, lo + per);
+    const int per = (K + G - 1) / G;
+    const int lo = g * per;
+    const int hi = min(K, lo + per);
     for (int idx = lo + (int)threadIdx.x; idx < hi; idx += blockDim.x) {
-        double s = MAX ? -INFINITY : 0.0;
-        for (int q = 0; q < G; ++q) {
-            double v = cl.map_shared_rank(part, q)[idx];
-            s = MAX ? fmax(s, v) : s + v;
-        }
+        double v[kMaxCluster];
+#pragma unroll
+        for (int q = 0; q < kMaxCluster; ++q)
+            v[q] = (q < G) ? cl.map_shared_rank(part, q)[idx] : (MAX ? -INFINITY : 0.0);
+        double s = v[0];
+#pragma unroll
+        for (int q = 1; q < kMaxCluster; ++q) s = MAX ? fmax(s, v[q]) : s + v[q];
         for (int q = 0; q < G; ++q) cl.map_shared_rank(out, q)[idx] = s;
     }
     cl.sync();
 }
 
 // Block-wide sum (or max) of NV doubles held by every thread; thread i < NV
-// writes dst[i].  Ends with __syncthreads.
+// writes dst[i].  Ends with __syncthreads.  (Used outside the inner loop.)
 template <int NV, bool MAX = false>
 __device__ void block_reduce(double (&v)[NV], double* dst, double* wred, int lane, int warp) {
 #pragma unroll
@@ -210,46 +251,68 @@ __device__ void block_reduce(double (&v)[NV], double* dst, double* wred, int lan
     __syncthreads();
 }
 
+// error-free float transformations (Knuth TwoSum) for double-float warp sums
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bhi, float blo) {
+    float s, e;
+    two_sum(hi, bhi, s, e);
+    e += lo + blo;
+    hi = s + e;
+    lo = e - (hi - s);
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// chunk geometry of the reduce pass: PCT periods x CH assets staged per step
+template <int PCT> struct Chunk { static constexpr int CH = 512 / PCT; };
+
 // ---------------------------------------------------------------------------
-// reduce pass over one chunk of periods [p0, p0 + pc), pc <= kPC:
+// reduce pass over one chunk of periods [p0, p0 + pc), pc <= PCT:
 //   vpart[q*Lr + j]          = sum_i A_ji a0_{p0+q, i}          (j < m)
 //   vpart[q*Lr + m + j]      = sum_i A_ji a1_{p0+q, i}
 //   vpart[q*Lr + 2m + j]     = sum_i F_ij (f0_{p0+q, i} - c_i)   (j < k)
 //   vpart[q*Lr + 2m + k + j] = sum_i F_ij (f1_{p0+q, i} - c_i)
 // with Lr = 2m + 2k, over the CTA's assets.  Thread per output row (asset-major
-// panels: consecutive rows are contiguous), vectors staged through shared
-// memory kCH assets at a time, products and chunk sums in M, chunk sums added
-// in FP64.  Null vectors give zeros.
+// panels: consecutive rows are contiguous, so a warp's loads coalesce), vectors
+// staged through shared memory CH assets at a time, products and chunk sums in
+// M, chunk sums added in FP64.  Null vectors give zeros.
 // ---------------------------------------------------------------------------
-template <class M, class S>
-__device__ void reduce_chunk(Ctx<M, S>& c, int p0, int pc, const double* a0, const double* a1,
-                             const double* f0, const double* f1, bool subcen) {
+template <int PCT, class M, class S>
+__device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, const double* a1,
+                               const double* f0, const double* f1, bool subcen) {
+    constexpr int CH = Chunk<PCT>::CH;
     const int m = c.m, k = c.k, np = c.np;
     const int rows = m + k;
     const int Lr = 2 * m + 2 * k;
     const S* Fam = c.I.Ft + (size_t)k * np;
     const S* Aam = c.I.At + (size_t)m * np;
-    M* st = c.stage;  // [4][kPC][kCH]
-    double acc[2][2][kPC];
+    M* st = c.stage;  // [4][PCT][CH]
+    double acc[2][2][PCT];
 #pragma unroll
     for (int s = 0; s < 2; ++s)
 #pragma unroll
         for (int t = 0; t < 2; ++t)
 #pragma unroll
-            for (int q = 0; q < kPC; ++q) acc[s][t][q] = 0;
-    for (int ib = c.i0; ib < c.i1; ib += kCH) {
-        const int cnt = min(kCH, c.i1 - ib);
-        for (int e = c.tid; e < 4 * kPC * kCH; e += kThreads) {
-            const int vec = e / (kPC * kCH);
-            const int q = (e / kCH) % kPC;
-            const int ii = e % kCH;
+            for (int q = 0; q < PCT; ++q) acc[s][t][q] = 0;
+    const bool has1 = (a1 != nullptr) || (f1 != nullptr);
+    for (int ib = c.i0; ib < c.i1; ib += CH) {
+        const int cnt = min(CH, c.i1 - ib);
+        for (int e = c.tid; e < 4 * PCT * CH; e += kThreads) {
+            const int vec = e / (PCT * CH);
+            const int q = (e / CH) % PCT;
+            const int ii = e % CH;
             double val = 0;
-            if (q < pc && ii < cnt) {
+            const double* src = vec == 0 ? a0 : vec == 1 ? a1 : vec == 2 ? f0 : f1;
+            if (src && q < pc && ii < cnt) {
                 const int i = ib + ii;
-                const size_t o = (size_t)(p0 + q) * np + i;
-                const double cc = (subcen && vec >= 2) ? c.I.cen[i] : 0.0;
-                const double* src = vec == 0 ? a0 : vec == 1 ? a1 : vec == 2 ? f0 : f1;
-                if (src) val = src[o] - cc;
+                val = src[(size_t)(p0 + q) * np + i] - ((subcen && vec >= 2) ? c.I.cen[i] : 0.0);
             }
             st[e] = (M)val;
         }
@@ -262,11 +325,11 @@ __device__ void reduce_chunk(Ctx<M, S>& c, int p0, int pc, const double* a0, con
                 const int j = isA ? row : row - m;
                 const S* base = isA ? (Aam + (size_t)ib * m + j) : (Fam + (size_t)ib * k + j);
                 const int stride = isA ? m : k;
-                const M* sv0 = st + (isA ? 0 : 2) * kPC * kCH;
-                const M* sv1 = st + (isA ? 1 : 3) * kPC * kCH;
-                M a[2][kPC];
+                const M* sv0 = st + (isA ? 0 : 2) * PCT * CH;
+                const M* sv1 = st + (isA ? 1 : 3) * PCT * CH;
+                M a[2][PCT];
 #pragma unroll
-                for (int q = 0; q < kPC; ++q) { a[0][q] = 0; a[1][q] = 0; }
+                for (int q = 0; q < PCT; ++q) { a[0][q] = 0; a[1][q] = 0; }
                 int ii = 0;
                 for (; ii + 8 <= cnt; ii += 8) {
                     M w[8];
@@ -275,21 +338,21 @@ __device__ void reduce_chunk(Ctx<M, S>& c, int p0, int pc, const double* a0, con
 #pragma unroll
                     for (int u = 0; u < 8; ++u)
 #pragma unroll
-                        for (int q = 0; q < kPC; ++q) {
-                            a[0][q] += w[u] * sv0[q * kCH + ii + u];
-                            a[1][q] += w[u] * sv1[q * kCH + ii + u];
+                        for (int q = 0; q < PCT; ++q) {
+                            a[0][q] += w[u] * sv0[q * CH + ii + u];
+                            if (has1) a[1][q] += w[u] * sv1[q * CH + ii + u];
                         }
                 }
                 for (; ii < cnt; ++ii) {
                     const M w = ldp<M, S>(base + (size_t)ii * stride);
 #pragma unroll
-                    for (int q = 0; q < kPC; ++q) {
-                        a[0][q] += w * sv0[q * kCH + ii];
-                        a[1][q] += w * sv1[q * kCH + ii];
+                    for (int q = 0; q < PCT; ++q) {
+                        a[0][q] += w * sv0[q * CH + ii];
+                        if (has1) a[1][q] += w * sv1[q * CH + ii];
                     }
                 }
 #pragma unroll
-                for (int q = 0; q < kPC; ++q) {
+                for (int q = 0; q < PCT; ++q) {
                     acc[s][0][q] += (double)a[0][q];
                     acc[s][1][q] += (double)a[1][q];
                 }
@@ -304,7 +367,7 @@ __device__ void reduce_chunk(Ctx<M, S>& c, int p0, int pc, const double* a0, con
             const bool isA = row < m;
             const int j = isA ? row : row - m;
 #pragma unroll
-            for (int q = 0; q < kPC; ++q) {
+            for (int q = 0; q < PCT; ++q) {
                 if (q < pc) {
                     if (isA) {
                         c.vpart[q * Lr + j] = acc[s][0][q];
@@ -320,136 +383,188 @@ __device__ void reduce_chunk(Ctx<M, S>& c, int p0, int pc, const double* a0, con
     __syncthreads();
 }
 
+template <class M, class S>
+__device__ void reduce_chunk(Ctx<M, S>& c, int p0, int pc, const double* a0, const double* a1, const double* f0,
+                             const double* f1, bool subcen) {
+    if (pc <= 1) reduce_chunk_t<1>(c, p0, pc, a0, a1, f0, f1, subcen);
+    else if (pc <= 2) reduce_chunk_t<2>(c, p0, pc, a0, a1, f0, f1, subcen);
+    else if (pc <= 4) reduce_chunk_t<4>(c, p0, pc, a0, a1, f0, f1, subcen);
+    else reduce_chunk_t<8>(c, p0, pc, a0, a1, f0, f1, subcen);
+}
+
 // ---------------------------------------------------------------------------
 // expand pass: for every local asset i and period p < Pv,
 //   epi(i, p, (F wF_p)_i, (A^T wA_p)_i)     with wF (Pv x k), wA (Pv x m)
-// arithmetic in A (M or double), factor-major panels.
+// arithmetic in A (M or double), factor-major panels (a warp's loads coalesce
+// along the assets).
 // ---------------------------------------------------------------------------
+template <int PCT, class A, class M, class S, class W, class Epi>
+__device__ void expand_chunk(Ctx<M, S>& c, int i, int p0, int pc, const W* wF, const W* wA, Epi& epi) {
+    const int m = c.m, k = c.k, np = c.np;
+    A aF[PCT], aA[PCT];
+#pragma unroll
+    for (int q = 0; q < PCT; ++q) { aF[q] = 0; aA[q] = 0; }
+    const W* wf = wF + (size_t)p0 * k;
+    const W* wa = wA + (size_t)p0 * m;
+    int j = 0;
+    for (; j + 4 <= k; j += 4) {
+        A f[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) f[u] = ldp<A, S>(c.I.Ft + (size_t)(j + u) * np + i);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < PCT; ++q) aF[q] += f[u] * (A)wf[q * k + j + u];
+    }
+    for (; j < k; ++j) {
+        const A f = ldp<A, S>(c.I.Ft + (size_t)j * np + i);
+#pragma unroll
+        for (int q = 0; q < PCT; ++q) aF[q] += f * (A)wf[q * k + j];
+    }
+    j = 0;
+    for (; j + 4 <= m; j += 4) {
+        A a[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) a[u] = ldp<A, S>(c.I.At + (size_t)(j + u) * np + i);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < PCT; ++q) aA[q] += a[u] * (A)wa[q * m + j + u];
+    }
+    for (; j < m; ++j) {
+        const A a = ldp<A, S>(c.I.At + (size_t)j * np + i);
+#pragma unroll
+        for (int q = 0; q < PCT; ++q) aA[q] += a * (A)wa[q * m + j];
+    }
+#pragma unroll
+    for (int q = 0; q < PCT; ++q)
+        if (q < pc) epi(i, p0 + q, (double)aF[q], (double)aA[q]);
+}
+
+// The weight vectors must have PCT rows readable past Pv: callers size the
+// replicated arrays for whole chunks (rows beyond Pv hold finite values).
 template <class A, class M, class S, class W, class Epi>
 __device__ void expand_pass(Ctx<M, S>& c, int Pv, const W* wF, const W* wA, Epi epi) {
-    const int m = c.m, k = c.k, np = c.np;
     for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
         for (int p0 = 0; p0 < Pv; p0 += kPC) {
             const int pc = min(kPC, Pv - p0);
-            A aF[kPC], aA[kPC];
-#pragma unroll
-            for (int q = 0; q < kPC; ++q) { aF[q] = 0; aA[q] = 0; }
-            const W* wf = wF + (size_t)p0 * k;
-            const W* wa = wA + (size_t)p0 * m;
-            int j = 0;
-            for (; j + 4 <= k; j += 4) {
-                A f[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) f[u] = ldp<A, S>(c.I.Ft + (size_t)(j + u) * np + i);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int q = 0; q < kPC; ++q)
-                        if (q < pc) aF[q] += f[u] * (A)wf[q * k + j + u];
-            }
-            for (; j < k; ++j) {
-                const A f = ldp<A, S>(c.I.Ft + (size_t)j * np + i);
-#pragma unroll
-                for (int q = 0; q < kPC; ++q)
-                    if (q < pc) aF[q] += f * (A)wf[q * k + j];
-            }
-            j = 0;
-            for (; j + 4 <= m; j += 4) {
-                A a[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) a[u] = ldp<A, S>(c.I.At + (size_t)(j + u) * np + i);
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int q = 0; q < kPC; ++q)
-                        if (q < pc) aA[q] += a[u] * (A)wa[q * m + j + u];
-            }
-            for (; j < m; ++j) {
-                const A a = ldp<A, S>(c.I.At + (size_t)j * np + i);
-#pragma unroll
-                for (int q = 0; q < kPC; ++q)
-                    if (q < pc) aA[q] += a * (A)wa[q * m + j];
-            }
-#pragma unroll
-            for (int q = 0; q < kPC; ++q)
-                if (q < pc) epi(i, p0 + q, (double)aF[q], (double)aA[q]);
+            if (pc <= 1) expand_chunk<1, A>(c, i, p0, pc, wF, wA, epi);
+            else if (pc <= 2) expand_chunk<2, A>(c, i, p0, pc, wF, wA, epi);
+            else if (pc <= 4) expand_chunk<4, A>(c, i, p0, pc, wF, wA, epi);
+            else expand_chunk<8, A>(c, i, p0, pc, wF, wA, epi);
         }
     }
 }
 
 // ---------------------------------------------------------------------------
 // l1-ball projection thresholds for every period of vector vv (P x np):
-// theta_p >= 0 with sum_i max(|v_pi| - theta_p, 0) = 1, or 0 if ||v_p||_1 <= 1.
-// Candidate-bracketing search in FP64: each round evaluates
-// S(theta) = sum max(|v| - theta, 0) and N(theta) = #{|v| > theta} at kCand
-// candidates per period; a Newton step from the largest candidate with S >= 1
-// is exact once no |v| lies between it and a candidate with S < 1.
+// theta_p >= 0 with S(theta) = sum_i max(|v_pi| - theta, 0) = 1, or 0 when
+// ||v_p||_1 <= 1 (projection onto the budget set of Eq. 3 / Eq. 6).
+// S is convex, decreasing and piecewise linear with breakpoints at the |v_i|.
+// Newton's method from the warm start t_0:
+//   t_{k+1} = (sum_{|v| > t_k} |v| - 1) / #{|v| > t_k}
+// lands at or below the root from any start (tangents of a convex function
+// lie below it).  When the count #{|v| > t} is the same at t_k and t_{k+1},
+// no breakpoint lies between them, S is linear there and t_{k+1} is the
+// root exactly.  FP64 sums; warp sums as error-free double-float pairs; the
+// per-warp partials are added in warp order (deterministic).
+// Returns the number of rounds (passes over v).
 // ---------------------------------------------------------------------------
 template <class M, class S>
-__device__ void l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const double* vv, double* th_out,
-                              double* th_warm) {
+__device__ int l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const double* vv, double* th_out,
+                             double* th_warm) {
     const int P = c.P, np = c.np;
-    double* cand = c.cand;
+    float* slotS = (float*)c.vpart;     // [kWarps][P][2]  (hi, lo)
+    int* slotN = (int*)c.vout;          // [kWarps][P]
     __shared__ int done_s[64];
-    for (int e = c.tid; e < P * kCand; e += kThreads) {
-        const int p = e / kCand, q = e % kCand;
-        const double w = th_warm[p];
-        const double f[kCand] = {0.0, 0.9, 0.99, 0.999, 1.0, 1.001, 1.01, 1.1};
-        cand[e] = (w > 0) ? w * f[q] : 0.0;
+    __shared__ double t_s[64];
+    __shared__ int nprev_s[64];
+    for (int p = c.tid; p < P; p += kThreads) {
+        done_s[p] = 0;
+        t_s[p] = th_warm[p] > 0 ? th_warm[p] : 0.0;
+        nprev_s[p] = -1;
     }
-    for (int p = c.tid; p < 64; p += kThreads) done_s[p] = 0;
     __syncthreads();
+    const bool wpp = P >= kWarps / 2;   // one warp per period, else all warps on every period
+    const int pstart = wpp ? c.warp : 0;
+    const int pstep = wpp ? kWarps : 1;
+    const int istart = wpp ? c.i0 + c.lane : c.i0 + c.tid;
+    const int istep = wpp ? 32 : kThreads;
+    const int nw = wpp ? 1 : kWarps;
+    int rounds_done = 0;
     for (int round = 0; round < kMaxRounds; ++round) {
-        for (int p = 0; p < P; ++p) {
-            double acc[2 * kCand];
+        for (int p = pstart; p < P; p += pstep) {
+            if (done_s[p]) continue;
+            const double* vp = vv + (size_t)p * np;
+            const double t = t_s[p];
+            double sd = 0;
+            int nd = 0;
+            for (int i = istart; i < c.i1; i += istep) {
+                const double a = fabs(vp[i]);
+                if (a > t) { sd += a; nd += 1; }
+            }
+            float hi = (float)sd;
+            float lo = (float)(sd - (double)hi);
 #pragma unroll
-            for (int q = 0; q < 2 * kCand; ++q) acc[q] = 0;
+            for (int o = 16; o > 0; o >>= 1) {
+                const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
+                const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
+                df_add(hi, lo, bh, bl);
+            }
+            const int nsum = __reduce_add_sync(0xffffffffu, nd);
+            if (c.lane == 0) {
+                const int slot = wpp ? p : (c.warp * P + p);
+                slotS[2 * slot] = hi;
+                slotS[2 * slot + 1] = lo;
+                slotN[slot] = nsum;
+            }
+        }
+        __syncthreads();
+        for (int p = c.tid; p < P; p += kThreads) {
+            double sv = 0, nn = 0;
             if (!done_s[p]) {
-                double cq[kCand];
-#pragma unroll
-                for (int q = 0; q < kCand; ++q) cq[q] = cand[p * kCand + q];
-                for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
-                    const double a = fabs(vv[(size_t)p * np + i]);
-#pragma unroll
-                    for (int q = 0; q < kCand; ++q) {
-                        const double dl = a - cq[q];
-                        if (dl > 0) { acc[q] += dl; acc[kCand + q] += 1.0; }
-                    }
+                for (int w = 0; w < nw; ++w) {
+                    const int slot = wpp ? p : (w * P + p);
+                    sv += (double)slotS[2 * slot] + (double)slotS[2 * slot + 1];
+                    nn += (double)slotN[slot];
                 }
             }
-            block_reduce<2 * kCand>(acc, c.spart + p * 2 * kCand, c.wred, c.lane, c.warp);
+            c.spart[2 * p] = sv;
+            c.spart[2 * p + 1] = nn;
         }
-        team_reduce<false>(cl, c.spart, c.sout, P * 2 * kCand, c.G, c.g);
+        team_reduce<false>(cl, c.spart, c.sout, 2 * P, c.G, c.g);
         if (c.tid == 0) {
             for (int p = 0; p < P; ++p) {
                 if (done_s[p]) continue;
-                const double* Sv = c.sout + p * 2 * kCand;
-                const double* Nv = Sv + kCand;
-                double* cp = cand + p * kCand;
-                if (round == 0 && Sv[0] <= 1.0) {   // inside the ball (candidate 0 is 0)
+                const double Sv = c.sout[2 * p];
+                const int Nv = (int)c.sout[2 * p + 1];
+                const double t = t_s[p];
+                if (t == 0.0 && Sv <= 1.0) {                   // inside the ball
                     th_out[p] = 0.0;
                     done_s[p] = 1;
                     continue;
                 }
-                int lo = -1, hi = -1;
-                for (int q = 0; q < kCand; ++q) {
-                    if (Sv[q] >= 1.0) { if (lo < 0 || cp[q] > cp[lo]) lo = q; }
-                    else { if (hi < 0 || cp[q] < cp[hi]) hi = q; }
+                if (Nv == nprev_s[p]) {                        // no breakpoint crossed: exact
+                    th_out[p] = t;
+                    done_s[p] = 1;
+                    continue;
                 }
-                if (lo < 0) lo = 0;
-                const double tl = cp[lo];
-                const double tn = tl + (Sv[lo] - 1.0) / fmax(Nv[lo], 1.0);
-                const bool exact = (hi >= 0 && Nv[hi] == Nv[lo]) || (Sv[lo] == 1.0);
-                if (exact || round == kMaxRounds - 1) {
+                double tn = (Sv - 1.0) / (double)(Nv > 0 ? Nv : 1);
+                if (tn <= 0.0) {                               // step from above past 0: test 0
+                    tn = 0.0;
+                    nprev_s[p] = -1;
+                } else {
+                    nprev_s[p] = Nv;
+                }
+                t_s[p] = tn;
+                if (round == kMaxRounds - 1) {                 // budget spent: a lower bound
                     th_out[p] = tn;
                     done_s[p] = 1;
-                } else {
-                    const double th = (hi >= 0) ? cp[hi] : fmax(tn * 1.5, tn + 1e-300);
-                    for (int q = 0; q < kCand; ++q) cp[q] = tn + (th - tn) * (double)q / (double)kCand;
                 }
             }
         }
         __syncthreads();
+        ++rounds_done;
         int rem = 0;
         for (int p = 0; p < P; ++p) rem += done_s[p] ? 0 : 1;
         if (rem == 0) break;
@@ -457,6 +572,7 @@ __device__ void l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const double*
     if (c.tid == 0)
         for (int p = 0; p < P; ++p) th_warm[p] = th_out[p];
     __syncthreads();
+    return rounds_done;
 }
 
 // om_p = Omega u_p for all periods, written as M (replicated in every CTA)
@@ -518,11 +634,20 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         c.cand = (double*)(smem + Ly.cand);
         c.thprev = (double*)(smem + Ly.thprev);
         c.theta = (double*)(smem + Ly.theta);
+        c.thq = (double*)(smem + Ly.thq);
         c.lb = (double*)(smem + Ly.lb);
         c.ubd = (double*)(smem + Ly.ubd);
         const double kap = c.I.kappa;
         const double dexp = c.I.d;
         const unsigned long long t_start = globaltimer();
+        double ph[6] = {0, 0, 0, 0, 0, 0};
+        unsigned long long tph = t_start;
+        auto lap = [&](int slot) {
+            const unsigned long long t = globaltimer();
+            ph[slot] += (double)(t - tph);
+            tph = t;
+        };
+        long long th_rounds = 0;
 
         // ---- prologue: replicated constants -------------------------------
         for (int e = c.tid; e < (c.I.omega_diag ? k : k * k); e += kThreads) c.Om[e] = c.I.Om[e];
@@ -580,6 +705,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         const double sig = (1.0 / tau - prm.beta * Lf) / ((m > 0) ? 2.0 : 1.0);
         const double sA = sig / nA2;
         const double sD = sig / nD2;
+        const double inv_sD = 1.0 / sD;
         const double rho = prm.rho;
 
         // ---- initial point: w0 (single) / straight line w0 -> w_T (multi) ----
@@ -602,7 +728,10 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             c.yAm[e] = (M)0;
             c.I.yA0[e] = 0;
         }
-        for (int p = c.tid; p < P; p += kThreads) c.thprev[p] = 0;
+        for (int p = c.tid; p < P; p += kThreads) {
+            c.thprev[p] = 0;
+            c.thq[p] = 0;
+        }
         __syncthreads();
         // u = F^T (x - c), ax = A x
         for (int p0 = 0; p0 < P; p0 += kPC) {
@@ -624,6 +753,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             aTwT = c.sout[0];
         }
 
+        lap(0);
         // ---- main loop ---------------------------------------------------------
         long long it = 0;
         int j = 0, restarts = 0;
@@ -641,17 +771,21 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                 const double* x = c.I.x;
                 const double* yD = c.I.yD;
                 double* v = c.I.v;
+                const M kapm = (M)kap;
                 expand_pass<M>(c, P, c.om, c.yAm, [&](int i, int p, double aF, double aA) {
+                    // gradient and K^T y in M; the state update in FP64
                     const size_t o = (size_t)p * np + i;
                     const double xv = x[o];
-                    const double gf = -c.I.alpha[o] + 2.0 * kap * (aF + c.I.Dp[o] * (xv - c.I.cen[i]));
-                    const double kt = aA + yD[o] - ((p + 1 < R) ? yD[o + np] : 0.0);
-                    v[o] = xv - tau * (gf + kt);
+                    const M gf = -(M)c.I.alpha[o] + (M)2 * kapm * ((M)aF + (M)c.I.Dp[o] * (M)(xv - c.I.cen[i]));
+                    const M kt = (M)aA + (M)yD[o] - ((p + 1 < R) ? (M)yD[o + np] : (M)0);
+                    v[o] = xv - tau * (double)(gf + kt);
                 });
             }
             __syncthreads();
+            lap(1);
             // (3) thresholds of the l1 projection
-            l1_thresholds(cl, c, c.I.v, c.theta, c.thprev);
+            th_rounds += l1_thresholds(cl, c, c.I.v, c.theta, c.thprev);
+            lap(2);
             // (4) elementwise: x_bar, y_D bar, Halpern combination, residual parts
             double rloc[2] = {0, 0};
             {
@@ -680,9 +814,11 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                         const size_t orr = (size_t)r * np + i;
                         const double yd = c.I.yD[orr];
                         const double pD = yd + sD * dxe;
-                        const double t = pD / sD + b;
-                        const double pr = prox_cost(t, 1.0 / sD, c.I.c1[orr], c.I.c2[orr], dexp);
-                        const double ydb = pD - sD * (pr - b);
+                        const double t = pD * inv_sD + b;
+                        M ylive;
+                        const double ydb = trade_multiplier<M>(t, inv_sD, c.I.c1[orr], c.I.c2[orr], dexp, ylive)
+                                               ? (double)ylive
+                                               : pD + sD * b;
                         c.I.yDb[orr] = ydb;
                         c.I.yDn[orr] = cj * ((1.0 + rho) * ydb - rho * yd) + oj * c.I.yD0[orr];
                         if (check) rloc[1] += (yd - ydb) * (yd - ydb);
@@ -690,6 +826,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                 }
             }
             __syncthreads();
+            lap(3);
             // (5) reduce per chunk of periods: A x_bar, A x_new, F^T(x_new - c) [, F^T(x_bar - c)];
             //     then the replicated y_A update and Halpern on y_A
             double rA = 0, pin = 0, nAx = 0, nCl = 0;
@@ -733,6 +870,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                 double* t2 = c.I.yD; c.I.yD = c.I.yDn; c.I.yDn = t2;
             }
             ++j;
+            lap(4);
             if (!check) continue;
 
             // ---- (6) check: fixed-point residual and relative KKT at T(z), FP64 ----
@@ -828,11 +966,9 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             double gstar = 0;
             for (int p = 0; p < P; ++p) gstar += c.sout[p];
             __syncthreads();
-            // stationarity residual ||x_bar - Proj(q)||  (projection thresholds, cold start)
-            if (c.tid == 0)
-                for (int p = 0; p < P; ++p) c.theta[p] = 0.0;
-            __syncthreads();
-            l1_thresholds(cl, c, c.I.v, c.theta, c.theta);
+            // stationarity residual ||x_bar - Proj(q)||  (thresholds warm-started
+            // from the previous check)
+            l1_thresholds(cl, c, c.I.v, c.theta, c.thq);
             double dr[1] = {0};
             for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
                 for (int p = 0; p < P; ++p) {
@@ -865,6 +1001,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             const double fpr = sqrt(sums[0] / tau + sums[1] / sD + rA_t / sA);
             res_rel = rel; res_p = r_p; res_d = r_d; res_g = r_g; res_P = Pobj; res_D = Dobj;
             r_last = fpr;
+            lap(5);
             if (!(rel == rel) || !(fpr == fpr)) { status = FF_NUMERICAL; break; }
             if (rel <= prm.tol) { status = FF_CONVERGED; break; }
             if (sums[9] > prm.time_limit_ns) { status = FF_TIME_LIMIT; break; }
@@ -926,6 +1063,8 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             rs.fixed_point_res = r_last;
             rs.seconds = (double)(globaltimer() - t_start) * 1e-9;
             rs.lipschitz = Lf;
+            rs.threshold_rounds = th_rounds;
+            for (int q = 0; q < 6; ++q) rs.phase_seconds[q] = ph[q] * 1e-9;
             *c.I.res = rs;
         }
         // the next instance reuses shared memory: every rank must be done with it

@@ -33,7 +33,7 @@ def test_exports(lib):
 
 def test_struct_sizes_match_header(lib):
     # ff_result layout mirrors the header (all 8-byte fields after two int32)
-    assert C.sizeof(_lib.ff_result) == 4 + 4 + 8 + 8 * 10
+    assert C.sizeof(_lib.ff_result) == 4 + 4 + 8 + 8 * 10 + 8 + 8 * 6
     assert _lib.RESULT_DTYPE.itemsize == C.sizeof(_lib.ff_result)
 
 
