@@ -112,6 +112,10 @@ typedef struct ff_options {
     double  beta;               /* dual steps sigma_i ||K_i||^2 sum to 1/tau - beta L_f, so the
                                    smooth part is (beta)-cocoercive in the step metric; beta > 1/2,
                                    default 0.75 */
+    int32_t reuse_workspace;    /* 1: ws already holds the repacked data of exactly these
+                                   problems from the previous call with the same ws (same
+                                   arrays, same values); the repack step is skipped and only
+                                   the solver runs.  Default 0. */
 } ff_options;
 
 /* Per-instance outcome, written to DEVICE memory by the solve calls. */

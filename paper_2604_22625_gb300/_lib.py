@@ -52,7 +52,7 @@ class ff_options(C.Structure):
                 ("precision", C.c_int32), ("check_every", C.c_int32), ("reflection", C.c_double),
                 ("restart_sufficient", C.c_double), ("restart_necessary", C.c_double),
                 ("step_fraction", C.c_double), ("cluster_size", C.c_int32), ("max_teams", C.c_int32),
-                ("beta", C.c_double)]
+                ("beta", C.c_double), ("reuse_workspace", C.c_int32)]
 
 
 class ff_result(C.Structure):

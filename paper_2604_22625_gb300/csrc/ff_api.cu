@@ -93,6 +93,7 @@ void fill_defaults(ff_options* o) {
     o->restart_necessary = 0.8;
     o->step_fraction = 0.4;
     o->beta = 0.75;
+    o->reuse_workspace = 0;
     o->cluster_size = 0;
     o->max_teams = 0;
 }
@@ -271,6 +272,7 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
         int t = order[slot];
         table[slot] = carve<M, S>(probs[t], sz[t], cur, w_out[t], yA_out ? yA_out[t] : nullptr,
                                      yD_out ? yD_out[t] : nullptr, res + t);
+        if (o.reuse_workspace) continue;
         const ff_problem& p = probs[t];
         int blocks = (int)std::min<long long>(1024, ((long long)sz[t].np * std::max(sz[t].k, 1) + 255) / 256 + 1);
         if (p.dtype == FF_F64)
@@ -280,9 +282,12 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return FF_ERR_CUDA;
     }
-    cudaError_t e = cudaMemcpyAsync(table_dev, table.data(), (size_t)count * sizeof(Inst<M, S>),
-                                    cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return FF_ERR_CUDA;
+    cudaError_t e = cudaSuccess;
+    if (!o.reuse_workspace) {
+        e = cudaMemcpyAsync(table_dev, table.data(), (size_t)count * sizeof(Inst<M, S>), cudaMemcpyHostToDevice,
+                            stream);
+        if (e != cudaSuccess) return FF_ERR_CUDA;
+    }
     int G = o.cluster_size > 0 ? o.cluster_size : auto_cluster(sz[order[0]], count);
     int maxc = 0;
     e = max_teams<M, S>(G, smem, &maxc);
