@@ -159,14 +159,18 @@ int ff_solve_multi(const ff_problem* p, const ff_options* o, void* ws, size_t ws
                    ff_result* result_dev, void* w_out, void* yA_out, void* yD_out, void* stream);
 
 /* Solve `count` independent instances (single- and multi-period mixed) in one
- * persistent launch.  probs is a HOST array of count problems; w_out is a HOST
- * array of count DEVICE pointers (layout as above); result_dev is a device
- * array of count ff_result. */
+ * persistent launch.  probs is a HOST array of count problems (1 <= count <=
+ * 65535); w_out is a HOST array of count DEVICE pointers (layout as above);
+ * result_dev is a device array of count ff_result. */
 int ff_solve_batch(const ff_problem* probs, int count, const ff_options* o, void* ws, size_t ws_bytes,
                    ff_result* result_dev, void* const* w_out, void* stream);
 
 /* Message for an FF_* return code (static storage). */
 const char* ff_status_string(int code);
+
+/* Description of the CUDA runtime call that made the last FF_ERR_CUDA return
+ * on the calling host thread ("" if none); static thread-local storage. */
+const char* ff_last_error(void);
 
 /* ABI version (major * 10000 + minor * 100 + patch). */
 int ff_version(void);

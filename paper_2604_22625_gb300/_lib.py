@@ -70,7 +70,7 @@ RESULT_DTYPE = np.dtype([(name, {C.c_int32: np.int32, C.c_int64: np.int64, C.c_d
 assert RESULT_DTYPE.itemsize == C.sizeof(ff_result)
 
 EXPORTS = ("ff_default_options", "ff_workspace_size", "ff_solve_single", "ff_solve_multi",
-           "ff_solve_batch", "ff_status_string", "ff_version")
+           "ff_solve_batch", "ff_status_string", "ff_version", "ff_last_error")
 
 _lib = None
 
@@ -97,6 +97,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.ff_solve_batch.restype = C.c_int
     lib.ff_status_string.argtypes = [C.c_int]
     lib.ff_status_string.restype = C.c_char_p
+    lib.ff_last_error.argtypes = []
+    lib.ff_last_error.restype = C.c_char_p
     lib.ff_version.argtypes = []
     lib.ff_version.restype = C.c_int
     _lib = lib
@@ -138,6 +140,10 @@ def ff_solve_batch(probs, count: int, opts: ff_options, ws: int, ws_bytes: int, 
 
 def ff_status_string(code: int) -> str:
     return load().ff_status_string(code).decode()
+
+
+def ff_last_error() -> str:
+    return load().ff_last_error().decode()
 
 
 def ff_version() -> int:

@@ -110,7 +110,7 @@ def solve(prob, precision: str = "f32", device: str = "cuda", return_duals: bool
     rc = fn(dp.struct, opts, ws.data_ptr(), ws_bytes, res.data_ptr(), w.data_ptr(),
             yA.data_ptr() if yA is not None else 0, yD.data_ptr() if yD is not None else 0, s.cuda_stream)
     if rc != L.FF_OK:
-        raise RuntimeError(f"solve failed: {L.ff_status_string(rc)} ({rc})")
+        raise RuntimeError(f"solve failed: {L.ff_status_string(rc)} ({rc}) {L.ff_last_error()}")
     s.synchronize()
     rec = res.cpu().numpy().view(L.RESULT_DTYPE)[0]
     wn = w.cpu().numpy().astype(np.float64)
@@ -121,41 +121,139 @@ def solve(prob, precision: str = "f32", device: str = "cuda", return_duals: bool
                     _info(rec))
 
 
+_FIELDS = ("F", "Omega", "D", "alpha", "s", "q", "w0", "wT", "A", "L", "U")
+_ALIGN = 64   # elements: every packed array starts on a 256-byte boundary
+
+
+def _omega_arg(prob):
+    """(array, omega_diag): the diagonal of Omega when it has no off-diagonal entries."""
+    Om = np.asarray(prob.Omega, dtype=np.float64)
+    if Om.ndim == 2 and np.count_nonzero(Om - np.diag(np.diag(Om))) == 0:
+        return np.diag(Om), 1
+    return Om, 0
+
+
+def pack(problems: Sequence, np_dtype) -> tuple:
+    """Lay the arrays of every instance out in one flat host buffer.
+
+    Returns (flat, layout) where layout[i] maps a field name to (offset, size)
+    in elements of ``flat`` and carries ``omega_diag``.  One buffer means one
+    host-to-device copy for the whole batch."""
+    layout, chunks, off = [], [], 0
+    for p in problems:
+        ent = {}
+        multi = int(p.T) >= 2
+        for nm in _FIELDS:
+            if nm == "wT" and not multi:
+                continue
+            if nm == "Omega":
+                a, ent["omega_diag"] = _omega_arg(p)
+            else:
+                a = np.asarray(getattr(p, nm), dtype=np.float64)
+            a = a.reshape(-1)
+            ent[nm] = (off, a.size)
+            chunks.append((off, a))
+            off += (a.size + _ALIGN - 1) // _ALIGN * _ALIGN
+        layout.append(ent)
+    flat = np.zeros(max(off, 1), dtype=np_dtype)
+    for o, a in chunks:
+        flat[o:o + a.size] = a
+    return flat, layout
+
+
+def _struct(p, ent, base_ptr: int, elem: int, ff_dtype: int) -> L.ff_problem:
+    st = L.ff_problem()
+    multi = int(p.T) >= 2
+    st.n, st.k = int(p.F.shape[0]), int(p.F.shape[1])
+    st.m = int(np.asarray(p.A).shape[0])
+    st.T = int(p.T) if multi else 0
+    st.dtype = ff_dtype
+    st.omega_diag = ent["omega_diag"]
+    for nm in _FIELDS:
+        if nm in ent and ent[nm][1] > 0:
+            setattr(st, nm, base_ptr + ent[nm][0] * elem)
+        else:
+            setattr(st, nm, None)
+    st.GMV, st.lambda1, st.lambda2, st.lambda3, st.d = (float(p.GMV), float(p.lam1), float(p.lam2),
+                                                         float(p.lam3), float(p.d))
+    return st
+
+
 class BatchRunner:
-    """Device-resident batch: inputs copied once, ``run()`` re-solves them all
-    in one persistent launch (what the throughput benchmark times)."""
+    """A batch packed into one device buffer; ``run()`` solves every instance
+    in one call of ``ff_solve_batch`` (what the throughput benchmark times).
+
+    ``run_from_host()`` is the end-to-end form: one copy of the packed inputs
+    from pinned host memory, the solve, and one copy of the portfolios and
+    results back to pinned host memory, all on one stream."""
 
     def __init__(self, problems: Sequence, precision: str = "bf16", device: str = "cuda", **opt_kw):
         self.precision = precision
+        self.device = torch.device(device)
         self.dtype = torch.float64 if precision == "f64" else torch.float32
-        self.dps: List[DeviceProblem] = [to_device(p, dtype=self.dtype, device=device) for p in problems]
-        self.count = len(self.dps)
-        self.structs = (L.ff_problem * self.count)(*[d.struct for d in self.dps])
+        np_dtype = np.float64 if precision == "f64" else np.float32
+        self.problems = list(problems)
+        self.count = len(self.problems)
+        flat, self.layout = pack(self.problems, np_dtype)
+        self.host_in = torch.from_numpy(flat).pin_memory() if torch.cuda.is_available() else torch.from_numpy(flat)
+        self.dev_in = self.host_in.to(self.device)
+        elem = self.dev_in.element_size()
+        ffd = L.FF_F64 if self.dtype == torch.float64 else L.FF_F32
+        base = self.dev_in.data_ptr()
+        self.structs = (L.ff_problem * self.count)(
+            *[_struct(p, e, base, elem, ffd) for p, e in zip(self.problems, self.layout)])
+        self.P = [int(p.T) - 1 if int(p.T) >= 2 else 1 for p in self.problems]
+        self.n = [int(p.F.shape[0]) for p in self.problems]
+        self.w_off = np.concatenate([[0], np.cumsum([(P * n + _ALIGN - 1) // _ALIGN * _ALIGN
+                                                     for P, n in zip(self.P, self.n)])]).astype(np.int64)
         self.opts = options(precision, **opt_kw)
         self.ws_bytes = L.ff_workspace_size(self.structs, self.count, self.opts)
         if self.ws_bytes == 0:
             raise ValueError("invalid problem or options")
-        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=device)
-        self.res = torch.zeros(L.RESULT_DTYPE.itemsize * self.count, dtype=torch.uint8, device=device)
-        self.w = [torch.empty(d.P * d.n, dtype=self.dtype, device=device) for d in self.dps]
-        self.w_ptrs = [t.data_ptr() for t in self.w]
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.res = torch.zeros(L.RESULT_DTYPE.itemsize * self.count, dtype=torch.uint8, device=self.device)
+        self.w_dev = torch.empty(int(self.w_off[-1]), dtype=self.dtype, device=self.device)
+        welem = self.w_dev.element_size()
+        self.w_ptrs = [self.w_dev.data_ptr() + int(o) * welem for o in self.w_off[:-1]]
+        pin = torch.cuda.is_available()
+        self.w_host = torch.empty(self.w_dev.shape, dtype=self.dtype, pin_memory=pin)
+        self.res_host = torch.empty(self.res.shape, dtype=torch.uint8, pin_memory=pin)
+
+    @property
+    def h2d_bytes(self) -> int:
+        return self.host_in.numel() * self.host_in.element_size()
+
+    @property
+    def d2h_bytes(self) -> int:
+        return self.w_dev.numel() * self.w_dev.element_size() + self.res.numel()
 
     def run(self, stream: Optional[torch.cuda.Stream] = None) -> None:
-        s = stream if stream is not None else torch.cuda.current_stream()
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
         rc = L.ff_solve_batch(self.structs, self.count, self.opts, self.ws.data_ptr(), self.ws_bytes,
                               self.res.data_ptr(), self.w_ptrs, s.cuda_stream)
         if rc != L.FF_OK:
-            raise RuntimeError(f"batch solve failed: {L.ff_status_string(rc)} ({rc})")
+            raise RuntimeError(f"batch solve failed: {L.ff_status_string(rc)} ({rc}) {L.ff_last_error()}")
+
+    def run_from_host(self, stream: Optional[torch.cuda.Stream] = None) -> None:
+        """Copy the packed inputs from pinned host memory, solve, copy the
+        portfolios and results back (asynchronous on ``stream``)."""
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.stream(s):
+            self.dev_in.copy_(self.host_in, non_blocking=True)
+            self.run(s)
+            self.w_host.copy_(self.w_dev, non_blocking=True)
+            self.res_host.copy_(self.res, non_blocking=True)
 
     def results(self) -> List[dict]:
         recs = self.res.cpu().numpy().view(L.RESULT_DTYPE)
         return [_info(r) for r in recs]
 
     def portfolios(self) -> List[np.ndarray]:
+        flat = self.w_dev.cpu().numpy().astype(np.float64)
         out = []
-        for d, t in zip(self.dps, self.w):
-            a = t.cpu().numpy().astype(np.float64)
-            out.append(a.reshape(d.P, d.n) if d.P > 1 or d.struct.T >= 2 else a)
+        for i, p in enumerate(self.problems):
+            a = flat[self.w_off[i]:self.w_off[i] + self.P[i] * self.n[i]]
+            out.append(a.reshape(self.P[i], self.n[i]) if int(p.T) >= 2 else a)
         return out
 
 

@@ -1,6 +1,7 @@
 // C ABI of the solver (declared in include/flashfolio.h): argument checks,
 // workspace carving, panel repacking and the launch of the team kernel.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -12,6 +13,15 @@ namespace ff {
 namespace {
 
 constexpr size_t kAlign = 256;
+
+// Text of the last failed CUDA call on this host thread (ff_last_error).
+thread_local char g_last_error[256] = "";
+
+int cuda_fail(cudaError_t e, const char* where) {
+    snprintf(g_last_error, sizeof(g_last_error), "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
+    cudaGetLastError();   // clear a non-sticky launch error so the caller's stream stays usable
+    return FF_ERR_CUDA;
+}
 
 inline size_t a256(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -54,10 +64,16 @@ size_t inst_bytes(const Sizes& s, int omega_diag, int precision) {
     return b;
 }
 
-size_t inst_struct_bytes(int precision) {
-    return precision == FF_PREC_F64 ? sizeof(Inst<double, double>)
-                                    : (precision == FF_PREC_F32 ? sizeof(Inst<float, float>)
-                                                                : sizeof(Inst<float, __nv_bfloat16>));
+// instance table + problem copies at the start of the workspace
+template <class M, class S>
+size_t table_bytes(int count) {
+    return a256((size_t)count * sizeof(Inst<M, S>)) + a256((size_t)count * sizeof(ff_problem));
+}
+
+size_t table_bytes_of(int precision, int count) {
+    return precision == FF_PREC_F64 ? table_bytes<double, double>(count)
+                                    : (precision == FF_PREC_F32 ? table_bytes<float, float>(count)
+                                                                : table_bytes<float, __nv_bfloat16>(count));
 }
 
 bool valid_problem(const ff_problem* p) {
@@ -125,7 +141,8 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_s<__nv_bfloat16>(double 
 }
 
 template <class In, class M, class S>
-__global__ void repack_kernel(ff_problem p, Inst<M, S> I, double lam2, double lam3) {
+__device__ void repack_one(const ff_problem& p, const Inst<M, S>& I, double lam2, double lam3, size_t tid,
+                           size_t nth) {
     const In* F = (const In*)p.F;
     const In* A = (const In*)p.A;
     const In* Om = (const In*)p.Omega;
@@ -138,8 +155,6 @@ __global__ void repack_kernel(ff_problem p, Inst<M, S> I, double lam2, double la
     const In* L = (const In*)p.L;
     const In* U = (const In*)p.U;
     const int n = I.n, k = I.k, m = I.m, P = I.P, R = I.R, np = I.np;
-    const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-    const size_t nth = (size_t)gridDim.x * blockDim.x;
     S* Ft = (S*)I.Ft;
     S* Fam = Ft + (size_t)k * np;
     S* At = (S*)I.At;
@@ -182,6 +197,20 @@ __global__ void repack_kernel(ff_problem p, Inst<M, S> I, double lam2, double la
         ((double*)I.cen)[i] = (double)((in && I.multi) ? (double)wT[i] : 0.0);
         if (I.multi) ((double*)I.alphaT)[i] = (double)(in ? (double)al[(size_t)P * n + i] : 0.0);
     }
+}
+
+// One launch repacks every instance of the batch: blockIdx.y selects the
+// table slot, the blocks along x stride over that instance's elements.
+template <class M, class S>
+__global__ void repack_batch_kernel(const ff_problem* __restrict__ probs, const Inst<M, S>* __restrict__ insts) {
+    const ff_problem p = probs[blockIdx.y];
+    const Inst<M, S> I = insts[blockIdx.y];
+    const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    const size_t nth = (size_t)gridDim.x * blockDim.x;
+    if (p.dtype == FF_F64)
+        repack_one<double, M, S>(p, I, p.lambda2, p.lambda3, tid, nth);
+    else
+        repack_one<float, M, S>(p, I, p.lambda2, p.lambda3, tid, nth);
 }
 
 template <class M, class S>
@@ -243,7 +272,7 @@ template <class M, class S>
 int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_t ws_bytes, ff_result* res,
         void* const* w_out, void* const* yA_out, void* const* yD_out, cudaStream_t stream) {
     std::vector<Sizes> sz(count);
-    size_t need = a256((size_t)count * sizeof(Inst<M, S>));
+    size_t need = table_bytes<M, S>(count);
     size_t smem = 0;
     long long maxwork = 0;
     int maxn = 0;
@@ -251,7 +280,8 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
         sz[t] = sizes_of(probs[t]);
         if (!supported(sz[t], probs[t].omega_diag, o.precision)) return FF_ERR_UNSUPPORTED;
         need += inst_bytes(sz[t], probs[t].omega_diag, o.precision);
-        smem = std::max(smem, solver_smem_bytes(sz[t].P, sz[t].k, sz[t].m, probs[t].omega_diag, sizeof(double)));
+        smem = std::max(smem, solver_smem_bytes(sz[t].P, sz[t].k, sz[t].m, probs[t].omega_diag,
+                                                matvec_elem(o.precision)));
         maxn = std::max(maxn, sz[t].n * sz[t].P);
         maxwork = std::max(maxwork, (long long)sz[t].n * sz[t].P * (sz[t].k + sz[t].m));
     }
@@ -265,33 +295,34 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
         return wa > wb;
     });
     unsigned char* base = (unsigned char*)ws;
+    // table region: count Inst records, then count ff_problem records (slot order)
     Inst<M, S>* table_dev = (Inst<M, S>*)base;
-    unsigned char* cur = base + a256((size_t)count * sizeof(Inst<M, S>));
-    std::vector<Inst<M, S>> table(count);
+    ff_problem* probs_dev = (ff_problem*)(base + a256((size_t)count * sizeof(Inst<M, S>)));
+    unsigned char* cur = base + table_bytes<M, S>(count);
+    std::vector<unsigned char> staging(table_bytes<M, S>(count));
+    Inst<M, S>* table = (Inst<M, S>*)staging.data();
+    ff_problem* pslot = (ff_problem*)(staging.data() + a256((size_t)count * sizeof(Inst<M, S>)));
+    long long maxel = 1;
     for (int slot = 0; slot < count; ++slot) {
         int t = order[slot];
         table[slot] = carve<M, S>(probs[t], sz[t], cur, w_out[t], yA_out ? yA_out[t] : nullptr,
-                                     yD_out ? yD_out[t] : nullptr, res + t);
-        if (o.reuse_workspace) continue;
-        const ff_problem& p = probs[t];
-        int blocks = (int)std::min<long long>(1024, ((long long)sz[t].np * std::max(sz[t].k, 1) + 255) / 256 + 1);
-        if (p.dtype == FF_F64)
-            repack_kernel<double, M, S><<<blocks, 256, 0, stream>>>(p, table[slot], p.lambda2, p.lambda3);
-        else
-            repack_kernel<float, M, S><<<blocks, 256, 0, stream>>>(p, table[slot], p.lambda2, p.lambda3);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return FF_ERR_CUDA;
+                                  yD_out ? yD_out[t] : nullptr, res + t);
+        pslot[slot] = probs[t];
+        maxel = std::max(maxel, (long long)sz[t].np * std::max(std::max(sz[t].k, sz[t].m), sz[t].P + sz[t].R));
     }
     cudaError_t e = cudaSuccess;
     if (!o.reuse_workspace) {
-        e = cudaMemcpyAsync(table_dev, table.data(), (size_t)count * sizeof(Inst<M, S>), cudaMemcpyHostToDevice,
-                            stream);
-        if (e != cudaSuccess) return FF_ERR_CUDA;
+        e = cudaMemcpyAsync(base, staging.data(), staging.size(), cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy of the instance table");
+        const int bx = (int)std::min<long long>(64, (maxel + 255) / 256);
+        repack_batch_kernel<M, S><<<dim3((unsigned)bx, (unsigned)count), 256, 0, stream>>>(probs_dev, table_dev);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "repack launch");
     }
     int G = o.cluster_size > 0 ? o.cluster_size : auto_cluster(sz[order[0]], count);
     int maxc = 0;
     e = max_teams<M, S>(G, smem, &maxc);
-    if (e != cudaSuccess) return FF_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query of the solver kernel");
     if (maxc < 1) return FF_ERR_UNSUPPORTED;
     int nteams = std::min(count, maxc);
     if (o.max_teams > 0) nteams = std::min(nteams, o.max_teams);
@@ -307,7 +338,7 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
     prm.beta = o.beta;
     prm.power_iters = 60;
     e = launch_solver<M, S>(table_dev, count, prm, G, nteams, smem, stream);
-    if (e != cudaSuccess) return FF_ERR_CUDA;
+    if (e != cudaSuccess) return cuda_fail(e, "solver launch");
     (void)maxn;
     (void)maxwork;
     return FF_OK;
@@ -316,6 +347,7 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
 int dispatch(const ff_problem* probs, int count, const ff_options* o_in, void* ws, size_t ws_bytes,
              ff_result* res, void* const* w_out, void* const* yA_out, void* const* yD_out, void* stream) {
     if (count < 1 || !probs || !res || !w_out) return FF_ERR_INVALID_ARG;
+    if (count > 65535) return FF_ERR_UNSUPPORTED;   // one grid row per instance in the repack launch
     ff_options o;
     if (o_in) o = *o_in; else fill_defaults(&o);
     if (!valid_options(o)) return FF_ERR_INVALID_ARG;
@@ -347,7 +379,7 @@ size_t ff_workspace_size(const ff_problem* probs, int count, const ff_options* o
     ff_options o;
     if (o_in) o = *o_in; else ff::fill_defaults(&o);
     if (!ff::valid_options(o)) return 0;
-    size_t need = ff::a256((size_t)count * ff::inst_struct_bytes(o.precision));
+    size_t need = ff::table_bytes_of(o.precision, count);
     for (int t = 0; t < count; ++t) {
         if (!ff::valid_problem(&probs[t])) return 0;
         need += ff::inst_bytes(ff::sizes_of(probs[t]), probs[t].omega_diag, o.precision);
@@ -391,5 +423,7 @@ const char* ff_status_string(int code) {
 }
 
 int ff_version(void) { return 100; }
+
+const char* ff_last_error(void) { return ff::g_last_error; }
 
 }  // extern "C"
