@@ -165,6 +165,39 @@ int ff_solve_multi(const ff_problem* p, const ff_options* o, void* ws, size_t ws
 int ff_solve_batch(const ff_problem* probs, int count, const ff_options* o, void* ws, size_t ws_bytes,
                    ff_result* result_dev, void* const* w_out, void* stream);
 
+/* Size of the library-owned workspace used by ff_solve_single_static (32 MiB). */
+#define FF_STATIC_WORKSPACE_BYTES (32u * 1024u * 1024u)
+
+/* ff_solve_single_static: ff_solve_single without a caller workspace and
+ * without any allocation.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory at solve time, for
+ * example a host application or plugin framework that has reserved all
+ * device memory up front and hands out only fixed buffers, or a
+ * latency-critical loop where the implicit device synchronisation of
+ * cudaMalloc / cudaFree is not acceptable.
+ *
+ * Arguments, layouts and results are those of ff_solve_single (the caller
+ * still passes the problem arrays, result_dev and the outputs as device
+ * pointers).  The workspace is a file-scope device array of
+ * FF_STATIC_WORKSPACE_BYTES inside this library, which every GPU that loads
+ * the library holds until the process exits.  The call makes no cudaMalloc,
+ * cudaFree or other allocating call on the host or the device.
+ *
+ * - Problems whose workspace (ff_workspace_size for this one instance plus a
+ *   few hundred bytes of instance record) exceeds FF_STATIC_WORKSPACE_BYTES
+ *   are rejected with FF_ERR_WORKSPACE before anything is enqueued;
+ *   ff_last_error() then states the bytes needed.
+ * - The first call on each device looks up the array's device address with
+ *   cudaGetSymbolAddress (with that device current) and caches it; make that
+ *   first call before any stream capture.
+ * - Every call on a device shares the one array, and it keeps the previous
+ *   call's contents (nothing in it needs to start at zero: each solve writes
+ *   every region before reading it).  Calls that overlap on the GPU (other
+ *   streams, or other host threads) race on it: serialise them.
+ * Returns FF_OK or an FF_ERR_* code, like ff_solve_single. */
+int ff_solve_single_static(const ff_problem* p, const ff_options* o, ff_result* result_dev,
+                           void* w_out, void* yA_out, void* yD_out, void* stream);
+
 /* Message for an FF_* return code (static storage). */
 const char* ff_status_string(int code);
 

@@ -33,6 +33,8 @@ FF_PREC_F64 = 0
 FF_PREC_F32 = 1
 FF_PREC_BF16 = 2
 
+FF_STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
+
 STATUS_NAMES = {FF_CONVERGED: "converged", FF_MAX_ITER: "max_iter", FF_TIME_LIMIT: "time_limit",
                 FF_NUMERICAL: "numerical"}
 
@@ -70,7 +72,8 @@ RESULT_DTYPE = np.dtype([(name, {C.c_int32: np.int32, C.c_int64: np.int64, C.c_d
 assert RESULT_DTYPE.itemsize == C.sizeof(ff_result)
 
 EXPORTS = ("ff_default_options", "ff_workspace_size", "ff_solve_single", "ff_solve_multi",
-           "ff_solve_batch", "ff_status_string", "ff_version", "ff_last_error")
+           "ff_solve_batch", "ff_status_string", "ff_version", "ff_last_error",
+           "ff_solve_single_static")
 
 _lib = None
 
@@ -92,6 +95,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     for name in ("ff_solve_single", "ff_solve_multi"):
         getattr(lib, name).argtypes = sig
         getattr(lib, name).restype = C.c_int
+    lib.ff_solve_single_static.argtypes = [C.POINTER(ff_problem), C.POINTER(ff_options), C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.ff_solve_single_static.restype = C.c_int
     lib.ff_solve_batch.argtypes = [C.POINTER(ff_problem), C.c_int, C.POINTER(ff_options), C.c_void_p,
                                    C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p), C.c_void_p]
     lib.ff_solve_batch.restype = C.c_int
@@ -129,6 +135,13 @@ def ff_solve_multi(prob: ff_problem, opts: ff_options, ws: int, ws_bytes: int, r
     return int(load().ff_solve_multi(C.byref(prob), C.byref(opts), C.c_void_p(ws), ws_bytes, C.c_void_p(res),
                                      C.c_void_p(w), C.c_void_p(yA or None), C.c_void_p(yD or None),
                                      C.c_void_p(stream or None)))
+
+
+def ff_solve_single_static(prob: ff_problem, opts: ff_options, res: int, w: int, yA: int = 0, yD: int = 0,
+                           stream: int = 0) -> int:
+    return int(load().ff_solve_single_static(C.byref(prob), C.byref(opts), C.c_void_p(res), C.c_void_p(w),
+                                             C.c_void_p(yA or None), C.c_void_p(yD or None),
+                                             C.c_void_p(stream or None)))
 
 
 def ff_solve_batch(probs, count: int, opts: ff_options, ws: int, ws_bytes: int, res: int, w_ptrs,

@@ -5,12 +5,21 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "ff_internal.cuh"
 
+// Workspace of ff_solve_single_static: FF_STATIC_WORKSPACE_BYTES of device
+// memory that every GPU which loads this library holds until the process
+// exits.  Host code must not take its address directly (the host-side name is
+// only a stand-in); it uses the address from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_static_ws[FF_STATIC_WORKSPACE_BYTES];
+
 namespace ff {
 namespace {
+
+constexpr int kMaxStaticDevices = 64;
 
 constexpr size_t kAlign = 256;
 
@@ -365,6 +374,108 @@ int dispatch(const ff_problem* probs, int count, const ff_options* o_in, void* w
     }
 }
 
+// ---------------------------------------------------------------------------
+// ff_solve_single_static: the single-period solve on a workspace that lives in
+// this library's own device memory (g_static_ws below), for callers that must
+// not allocate.  Nothing here allocates: the instance record is staged on the
+// host stack and the workspace address comes from cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+constexpr size_t c_a256(size_t x) { return (x + 255) / 256 * 256; }
+
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxStaticDevices] = {};
+
+// Device address of g_static_ws on the current device, looked up once per
+// device with that device current.  Returns nullptr (and records the CUDA
+// error) when the lookup fails.
+void* static_workspace() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { cuda_fail(e, "cudaGetDevice"); return nullptr; }
+    if (dev < 0 || dev >= kMaxStaticDevices) {
+        snprintf(g_last_error, sizeof(g_last_error), "device ordinal %d beyond the %d supported", dev,
+                 kMaxStaticDevices);
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_static_ws);
+        if (e != cudaSuccess) { cuda_fail(e, "cudaGetSymbolAddress of the static workspace"); return nullptr; }
+        g_static_ptr[dev] = ptr;
+    }
+    return g_static_ptr[dev];
+}
+
+template <class M, class S>
+int run_single_static(const ff_problem& p, const ff_options& o, ff_result* res, void* w_out, void* yA_out,
+                      void* yD_out, cudaStream_t stream) {
+    const Sizes sz = sizes_of(p);
+    if (!supported(sz, p.omega_diag, o.precision)) return FF_ERR_UNSUPPORTED;
+    constexpr size_t kInstBytes = c_a256(sizeof(Inst<M, S>));
+    constexpr size_t kStage = kInstBytes + c_a256(sizeof(ff_problem));
+    const size_t need = kStage + inst_bytes(sz, p.omega_diag, o.precision);
+    if (need > (size_t)FF_STATIC_WORKSPACE_BYTES) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "problem needs %zu bytes of workspace; the static workspace holds %zu", need,
+                 (size_t)FF_STATIC_WORKSPACE_BYTES);
+        return FF_ERR_WORKSPACE;
+    }
+    unsigned char* base = (unsigned char*)static_workspace();
+    if (!base) return FF_ERR_CUDA;
+    alignas(16) unsigned char staging[kStage];
+    memset(staging, 0, sizeof(staging));
+    unsigned char* cur = base + kStage;
+    Inst<M, S> inst = carve<M, S>(p, sz, cur, w_out, yA_out, yD_out, res);
+    memcpy(staging, &inst, sizeof(inst));
+    memcpy(staging + kInstBytes, &p, sizeof(ff_problem));
+    // every region the solver reads is written by the repack or by the
+    // solver's own initialisation, so nothing has to be cleared between calls
+    cudaError_t e = cudaMemcpyAsync(base, staging, kStage, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "copy of the instance record");
+    const Inst<M, S>* table_dev = (const Inst<M, S>*)base;
+    const ff_problem* prob_dev = (const ff_problem*)(base + kInstBytes);
+    long long maxel = (long long)sz.np * std::max(std::max(sz.k, sz.m), sz.P + sz.R);
+    const int bx = (int)std::min<long long>(64, (maxel + 255) / 256);
+    repack_batch_kernel<M, S><<<dim3((unsigned)std::max(bx, 1), 1u), 256, 0, stream>>>(prob_dev, table_dev);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "repack launch");
+    const size_t smem = solver_smem_bytes(sz.P, sz.k, sz.m, p.omega_diag, matvec_elem(o.precision));
+    const int G = o.cluster_size > 0 ? o.cluster_size : auto_cluster(sz, 1);
+    int maxc = 0;
+    e = max_teams<M, S>(G, smem, &maxc);
+    if (e != cudaSuccess) return cuda_fail(e, "occupancy query of the solver kernel");
+    if (maxc < 1) return FF_ERR_UNSUPPORTED;
+    Params prm;
+    prm.tol = o.tol;
+    prm.max_iter = o.max_iter;
+    prm.time_limit_ns = o.time_limit * 1e9;
+    prm.check_every = o.check_every;
+    prm.rho = o.reflection;
+    prm.beta_suff = o.restart_sufficient;
+    prm.beta_nec = o.restart_necessary;
+    prm.step_fraction = o.step_fraction;
+    prm.beta = o.beta;
+    prm.power_iters = 60;
+    e = launch_solver<M, S>(table_dev, 1, prm, G, 1, smem, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "solver launch");
+    return FF_OK;
+}
+
+int solve_single_static(const ff_problem* p, const ff_options* o_in, ff_result* res, void* w_out, void* yA_out,
+                        void* yD_out, void* stream) {
+    if (!p || p->T != 0 || !res || !w_out) return FF_ERR_INVALID_ARG;
+    ff_options o;
+    if (o_in) o = *o_in; else fill_defaults(&o);
+    if (!valid_options(o) || !valid_problem(p)) return FF_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (o.precision) {
+        case FF_PREC_F64: return run_single_static<double, double>(*p, o, res, w_out, yA_out, yD_out, st);
+        case FF_PREC_F32: return run_single_static<float, float>(*p, o, res, w_out, yA_out, yD_out, st);
+        default: return run_single_static<float, __nv_bfloat16>(*p, o, res, w_out, yA_out, yD_out, st);
+    }
+}
+
 }  // namespace
 }  // namespace ff
 
@@ -408,6 +519,11 @@ int ff_solve_multi(const ff_problem* p, const ff_options* o, void* ws, size_t ws
 int ff_solve_batch(const ff_problem* probs, int count, const ff_options* o, void* ws, size_t ws_bytes,
                    ff_result* result_dev, void* const* w_out, void* stream) {
     return ff::dispatch(probs, count, o, ws, ws_bytes, result_dev, w_out, nullptr, nullptr, stream);
+}
+
+int ff_solve_single_static(const ff_problem* p, const ff_options* o, ff_result* result_dev, void* w_out,
+                           void* yA_out, void* yD_out, void* stream) {
+    return ff::solve_single_static(p, o, result_dev, w_out, yA_out, yD_out, stream);
 }
 
 const char* ff_status_string(int code) {
