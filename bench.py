@@ -51,6 +51,8 @@ def parse_args(argv=None):
                     choices=["batch", "single_large", "multi", "single_small", "batch_profile"])
     ap.add_argument("--max-iter", type=int, default=0, help="iteration cap (profiling runs only)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-graph", action="store_true", help="call ff_solve_batch directly instead of "
+                    "replaying the captured CUDA graph")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-instance form")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the CPU baseline sample")
@@ -318,8 +320,12 @@ def run_ours(args):
     bpi = [algorithmic_bytes_per_iter(p, precision) for p in probs]
     resident_in = runner.h2d_bytes
 
+    use_graph = not args.no_graph
+    if use_graph:
+        runner.capture(stream)
+    step = runner.replay if use_graph else runner.run
     for _ in range(args.warmup):
-        runner.run(stream)
+        step(stream)
     torch.cuda.synchronize(dev)
 
     sampler = ClockSampler(local)
@@ -332,7 +338,7 @@ def run_ours(args):
     t_wall = time.perf_counter()
     for s in range(args.steps):
         ev[s][0].record(stream)
-        runner.run(stream)
+        step(stream)
         ev[s][1].record(stream)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t_wall
@@ -345,8 +351,10 @@ def run_ours(args):
     solved = sum(1 for i in infos if i["status"] == 0 and i["rel_kkt"] <= TOL)
     kkt_max = max(i["rel_kkt"] for i in infos)
     iters = [int(i["iterations"]) for i in infos]
+    inst_s = [float(i["seconds"]) for i in infos]
     alg_bytes = float(sum(b * it for b, it in zip(bpi, iters)))
 
+    launches_per_step = 1 + runner.solver_launches()
     t_max = max_over_ranks(dist, dev_s, dev)
     solved_all = sum_over_ranks(dist, float(solved * args.steps), dev)
     value = solved_all / t_max if t_max > 0 else 0.0
@@ -421,9 +429,11 @@ def run_ours(args):
                        "l2": f"inputs larger than L2 ({resident_in / 2**20:.0f} MiB packed inputs, "
                              f"{runner.ws_bytes / 2**20:.0f} MiB workspace vs {l2_mb:.0f} MiB L2)",
                        "parallelism": f"replicas x{ws} (one batch per GPU)" if ws > 1 else "1 GPU",
-                       "max_iter_cap": args.max_iter or None},
+                       "max_iter_cap": args.max_iter or None,
+                       "graph": use_graph},
             "solved": solved, "max_rel_kkt": kkt_max,
             "iterations_mean": float(statistics.mean(iters)),
+            "instance_seconds": {"sum": float(sum(inst_s)), "max": float(max(inst_s))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "team_kernel (+ the one repack launch in the same call)",
@@ -431,7 +441,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "plain_form": plain,
             "e2e": e2e,
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": launches_per_step * args.steps,
             "clocks": clocks,
             "step_ms": step_ms,
             "wall_s": wall,

@@ -107,15 +107,25 @@ typedef struct ff_options {
     double  restart_sufficient; /* default 0.2 */
     double  restart_necessary;  /* default 0.8 */
     double  step_fraction;      /* primal step tau = step_fraction * 2 / L_f, default 0.4 */
-    int32_t cluster_size;       /* CTAs per instance: 0 = automatic, else 1, 2, 4, 8 or 16 */
+    int32_t cluster_size;       /* CTAs per instance: 0 = automatic (see cta_work), else 1, 2, 4,
+                                   8 or 16 for every instance */
     int32_t max_teams;          /* batch: concurrent instance teams, 0 = as many as fit */
     double  beta;               /* dual steps sigma_i ||K_i||^2 sum to 1/tau - beta L_f, so the
                                    smooth part is (beta)-cocoercive in the step metric; beta > 1/2,
                                    default 0.75 */
-    int32_t reuse_workspace;    /* 1: ws already holds the repacked data of exactly these
-                                   problems from the previous call with the same ws (same
-                                   arrays, same values); the repack step is skipped and only
-                                   the solver runs.  Default 0. */
+    int32_t reuse_workspace;    /* 0 (default): copy the instance table to ws, repack, solve.
+                                   1: ws already holds the table and the repacked data of exactly
+                                   these problems from an earlier call with the same ws (same
+                                   arrays, same values): only the solver runs.
+                                   2: ws already holds the table (same problems, same pointers)
+                                   but the arrays may hold new values: repack and solve, with no
+                                   host-to-device copy (the call is then capturable in a CUDA
+                                   graph once a mode-0 call has run outside the capture). */
+    double  cta_work;           /* batch scheduling: asset-periods per CTA that decide each
+                                   instance's cluster size (smallest power of two G <= 16 with
+                                   n * P / G <= cta_work); default 8192.  Instances of equal G
+                                   form one persistent launch; the launches run concurrently
+                                   on library-owned streams forked from `stream`. */
 } ff_options;
 
 /* Per-instance outcome, written to DEVICE memory by the solve calls. */
@@ -197,6 +207,15 @@ int ff_solve_batch(const ff_problem* probs, int count, const ff_options* o, void
  * Returns FF_OK or an FF_ERR_* code, like ff_solve_single. */
 int ff_solve_single_static(const ff_problem* p, const ff_options* o, ff_result* result_dev,
                            void* w_out, void* yA_out, void* yD_out, void* stream);
+
+/* Host-only schedule of ff_solve_batch for these problems and options (no
+ * device work; it reads the SM count of the current device when one is
+ * present): cluster_out (HOST, count entries, may be NULL) receives each
+ * instance's CTAs per instance, launches_out (may be NULL) the number of
+ * persistent solver launches (one per distinct cluster size).  A cluster
+ * size that cannot be resident on the device is halved at solve time. */
+int ff_batch_plan(const ff_problem* probs, int count, const ff_options* o, int32_t* cluster_out,
+                  int32_t* launches_out);
 
 /* Message for an FF_* return code (static storage). */
 const char* ff_status_string(int code);

@@ -54,7 +54,7 @@ class ff_options(C.Structure):
                 ("precision", C.c_int32), ("check_every", C.c_int32), ("reflection", C.c_double),
                 ("restart_sufficient", C.c_double), ("restart_necessary", C.c_double),
                 ("step_fraction", C.c_double), ("cluster_size", C.c_int32), ("max_teams", C.c_int32),
-                ("beta", C.c_double), ("reuse_workspace", C.c_int32)]
+                ("beta", C.c_double), ("reuse_workspace", C.c_int32), ("cta_work", C.c_double)]
 
 
 class ff_result(C.Structure):
@@ -73,7 +73,7 @@ assert RESULT_DTYPE.itemsize == C.sizeof(ff_result)
 
 EXPORTS = ("ff_default_options", "ff_workspace_size", "ff_solve_single", "ff_solve_multi",
            "ff_solve_batch", "ff_status_string", "ff_version", "ff_last_error",
-           "ff_solve_single_static")
+           "ff_solve_single_static", "ff_batch_plan")
 
 _lib = None
 
@@ -95,6 +95,9 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     for name in ("ff_solve_single", "ff_solve_multi"):
         getattr(lib, name).argtypes = sig
         getattr(lib, name).restype = C.c_int
+    lib.ff_batch_plan.argtypes = [C.POINTER(ff_problem), C.c_int, C.POINTER(ff_options),
+                                  C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.ff_batch_plan.restype = C.c_int
     lib.ff_solve_single_static.argtypes = [C.POINTER(ff_problem), C.POINTER(ff_options), C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.ff_solve_single_static.restype = C.c_int
@@ -142,6 +145,16 @@ def ff_solve_single_static(prob: ff_problem, opts: ff_options, res: int, w: int,
     return int(load().ff_solve_single_static(C.byref(prob), C.byref(opts), C.c_void_p(res), C.c_void_p(w),
                                              C.c_void_p(yA or None), C.c_void_p(yD or None),
                                              C.c_void_p(stream or None)))
+
+
+def ff_batch_plan(probs, count: int, opts: ff_options):
+    """(cluster size per instance, number of solver launches) of ff_solve_batch."""
+    cl = (C.c_int32 * count)()
+    nl = C.c_int32(0)
+    rc = int(load().ff_batch_plan(probs, count, C.byref(opts), cl, C.byref(nl)))
+    if rc != FF_OK:
+        raise ValueError(f"ff_batch_plan: {ff_status_string(rc)}")
+    return list(cl), int(nl.value)
 
 
 def ff_solve_batch(probs, count: int, opts: ff_options, ws: int, ws_bytes: int, res: int, w_ptrs,

@@ -218,6 +218,14 @@ class BatchRunner:
         pin = torch.cuda.is_available()
         self.w_host = torch.empty(self.w_dev.shape, dtype=self.dtype, pin_memory=pin)
         self.res_host = torch.empty(self.res.shape, dtype=torch.uint8, pin_memory=pin)
+        self.graph = None
+
+    def plan(self):
+        """(cluster size per instance, solver launches per call)."""
+        return L.ff_batch_plan(self.structs, self.count, self.opts)
+
+    def solver_launches(self) -> int:
+        return self.plan()[1]
 
     @property
     def h2d_bytes(self) -> int:
@@ -234,13 +242,42 @@ class BatchRunner:
         if rc != L.FF_OK:
             raise RuntimeError(f"batch solve failed: {L.ff_status_string(rc)} ({rc}) {L.ff_last_error()}")
 
+    def capture(self, stream: Optional[torch.cuda.Stream] = None) -> None:
+        """Capture one solve of the batch (repack + persistent launches) in a
+        CUDA graph; ``replay()`` then re-solves from the current contents of
+        the device input buffer with a single graph launch.  The instance
+        table is uploaded by an ordinary call first (capture cannot copy from
+        pageable host memory); the captured call reuses it (mode 2)."""
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.run(s)
+        s.synchronize()
+        saved = self.opts.reuse_workspace
+        self.opts.reuse_workspace = 2
+        try:
+            cap = torch.cuda.Stream(self.device)
+            cap.wait_stream(s)
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph, stream=cap, capture_error_mode="thread_local"):
+                self.run(cap)
+            s.wait_stream(cap)
+        finally:
+            self.opts.reuse_workspace = saved
+
+    def replay(self, stream: Optional[torch.cuda.Stream] = None) -> None:
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.stream(s):
+            self.graph.replay()
+
     def run_from_host(self, stream: Optional[torch.cuda.Stream] = None) -> None:
         """Copy the packed inputs from pinned host memory, solve, copy the
         portfolios and results back (asynchronous on ``stream``)."""
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         with torch.cuda.stream(s):
             self.dev_in.copy_(self.host_in, non_blocking=True)
-            self.run(s)
+            if getattr(self, "graph", None) is not None:
+                self.graph.replay()
+            else:
+                self.run(s)
             self.w_host.copy_(self.w_dev, non_blocking=True)
             self.res_host.copy_(self.res, non_blocking=True)
 

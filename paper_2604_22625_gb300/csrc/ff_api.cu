@@ -74,9 +74,12 @@ size_t inst_bytes(const Sizes& s, int omega_diag, int precision) {
 }
 
 // instance table + problem copies at the start of the workspace
+constexpr size_t kQueueBytes = 256;   // per-group instance counters of the device queue
+constexpr int kMaxGroups = 5;         // cluster sizes 1, 2, 4, 8, 16
+
 template <class M, class S>
 size_t table_bytes(int count) {
-    return a256((size_t)count * sizeof(Inst<M, S>)) + a256((size_t)count * sizeof(ff_problem));
+    return a256((size_t)count * sizeof(Inst<M, S>)) + a256((size_t)count * sizeof(ff_problem)) + kQueueBytes;
 }
 
 size_t table_bytes_of(int precision, int count) {
@@ -119,6 +122,7 @@ void fill_defaults(ff_options* o) {
     o->step_fraction = 0.4;
     o->beta = 0.75;
     o->reuse_workspace = 0;
+    o->cta_work = 8192.0;
     o->cluster_size = 0;
     o->max_teams = 0;
 }
@@ -136,6 +140,8 @@ bool valid_options(const ff_options& o) {
     int g = o.cluster_size;
     if (!(g == 0 || g == 1 || g == 2 || g == 4 || g == 8 || g == 16)) return false;
     if (o.max_teams < 0) return false;
+    if (o.reuse_workspace < 0 || o.reuse_workspace > 2) return false;
+    if (!(o.cta_work >= 1.0)) return false;
     return true;
 }
 
@@ -268,73 +274,78 @@ Inst<M, S> carve(const ff_problem& p, const Sizes& s, unsigned char*& cur, void*
 }
 
 int auto_cluster(const Sizes& s, int count) {
-    if (count > 1) {
-        // batch: one CTA per instance keeps every SM busy with its own instance
-        return 1;
-    }
+    if (count > 1) return 1;
     int g = 1;
     while (g < 16 && (long long)s.n * s.P > (long long)g * 384) g *= 2;
     return g;
 }
 
-template <class M, class S>
-int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_t ws_bytes, ff_result* res,
-        void* const* w_out, void* const* yA_out, void* const* yD_out, cudaStream_t stream) {
-    std::vector<Sizes> sz(count);
-    size_t need = table_bytes<M, S>(count);
-    size_t smem = 0;
-    long long maxwork = 0;
-    int maxn = 0;
+// Cluster size of every instance of a batch.  Each instance starts with the
+// smallest power of two G that keeps its asset-periods per CTA at or below
+// cta_work; while the whole batch would occupy fewer than half the SMs, the
+// instance with the most work per CTA is split further (down to 384
+// asset-periods per CTA), so that a small batch, or one instance, still
+// spreads over the GPU.
+void choose_clusters(const std::vector<Sizes>& sz, double cta_work, int sms, std::vector<int>& G) {
+    const int count = (int)sz.size();
+    G.assign(count, 1);
+    long long total = 0;
     for (int t = 0; t < count; ++t) {
-        sz[t] = sizes_of(probs[t]);
-        if (!supported(sz[t], probs[t].omega_diag, o.precision)) return FF_ERR_UNSUPPORTED;
-        need += inst_bytes(sz[t], probs[t].omega_diag, o.precision);
-        smem = std::max(smem, solver_smem_bytes(sz[t].P, sz[t].k, sz[t].m, probs[t].omega_diag,
-                                                matvec_elem(o.precision)));
-        maxn = std::max(maxn, sz[t].n * sz[t].P);
-        maxwork = std::max(maxwork, (long long)sz[t].n * sz[t].P * (sz[t].k + sz[t].m));
+        const double ap = (double)sz[t].n * sz[t].P;
+        while (G[t] < 16 && ap > (double)G[t] * cta_work) G[t] *= 2;
+        total += G[t];
     }
-    if (!ws || ((uintptr_t)ws % kAlign) != 0 || ws_bytes < need) return FF_ERR_WORKSPACE;
-    // LPT order: largest estimated work first, dealt round-robin to the teams
-    std::vector<int> order(count);
-    for (int t = 0; t < count; ++t) order[t] = t;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        long long wa = (long long)sz[a].n * sz[a].P * (sz[a].k + sz[a].m);
-        long long wb = (long long)sz[b].n * sz[b].P * (sz[b].k + sz[b].m);
-        return wa > wb;
-    });
-    unsigned char* base = (unsigned char*)ws;
-    // table region: count Inst records, then count ff_problem records (slot order)
-    Inst<M, S>* table_dev = (Inst<M, S>*)base;
-    ff_problem* probs_dev = (ff_problem*)(base + a256((size_t)count * sizeof(Inst<M, S>)));
-    unsigned char* cur = base + table_bytes<M, S>(count);
-    std::vector<unsigned char> staging(table_bytes<M, S>(count));
-    Inst<M, S>* table = (Inst<M, S>*)staging.data();
-    ff_problem* pslot = (ff_problem*)(staging.data() + a256((size_t)count * sizeof(Inst<M, S>)));
-    long long maxel = 1;
-    for (int slot = 0; slot < count; ++slot) {
-        int t = order[slot];
-        table[slot] = carve<M, S>(probs[t], sz[t], cur, w_out[t], yA_out ? yA_out[t] : nullptr,
-                                  yD_out ? yD_out[t] : nullptr, res + t);
-        pslot[slot] = probs[t];
-        maxel = std::max(maxel, (long long)sz[t].np * std::max(std::max(sz[t].k, sz[t].m), sz[t].P + sz[t].R));
+    while (total < sms / 2) {
+        int best = -1;
+        double bw = 0;
+        for (int t = 0; t < count; ++t) {
+            const double per = (double)sz[t].n * sz[t].P / G[t];
+            if (G[t] < 16 && per > 2.0 * 384 && per > bw) { bw = per; best = t; }
+        }
+        if (best < 0) break;
+        total += G[best];
+        G[best] *= 2;
     }
-    cudaError_t e = cudaSuccess;
-    if (!o.reuse_workspace) {
-        e = cudaMemcpyAsync(base, staging.data(), staging.size(), cudaMemcpyHostToDevice, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "copy of the instance table");
-        const int bx = (int)std::min<long long>(64, (maxel + 255) / 256);
-        repack_batch_kernel<M, S><<<dim3((unsigned)bx, (unsigned)count), 256, 0, stream>>>(probs_dev, table_dev);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "repack launch");
+}
+
+// Side streams (one per cluster-size group; side[0] has the highest
+// priority) and fork/join events, created once per device under
+// g_streams_mu, which also serialises the fork/join enqueue.
+struct DeviceStreams {
+    bool ready = false;
+    cudaStream_t side[kMaxGroups];
+    cudaEvent_t fork;
+    cudaEvent_t join[kMaxGroups];
+};
+std::mutex g_streams_mu;
+DeviceStreams g_streams[kMaxStaticDevices];
+
+int device_streams(DeviceStreams** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxStaticDevices) return FF_ERR_UNSUPPORTED;
+    DeviceStreams& d = g_streams[dev];
+    if (!d.ready) {
+        int least = 0, greatest = 0;
+        e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (e != cudaSuccess) return cuda_fail(e, "stream priority range");
+        for (int i = 0; i < kMaxGroups; ++i) {
+            const int prio = std::max(greatest, least - (kMaxGroups - 1 - i));
+            e = cudaStreamCreateWithPriority(&d.side[i], cudaStreamNonBlocking, prio);
+            if (e != cudaSuccess) return cuda_fail(e, "side stream creation");
+            e = cudaEventCreateWithFlags(&d.join[i], cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(e, "event creation");
+        }
+        e = cudaEventCreateWithFlags(&d.fork, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "event creation");
+        d.ready = true;
     }
-    int G = o.cluster_size > 0 ? o.cluster_size : auto_cluster(sz[order[0]], count);
-    int maxc = 0;
-    e = max_teams<M, S>(G, smem, &maxc);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy query of the solver kernel");
-    if (maxc < 1) return FF_ERR_UNSUPPORTED;
-    int nteams = std::min(count, maxc);
-    if (o.max_teams > 0) nteams = std::min(nteams, o.max_teams);
+    *out = &d;
+    return FF_OK;
+}
+
+Params make_params(const ff_options& o) {
     Params prm;
     prm.tol = o.tol;
     prm.max_iter = o.max_iter;
@@ -346,10 +357,135 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
     prm.step_fraction = o.step_fraction;
     prm.beta = o.beta;
     prm.power_iters = 60;
-    e = launch_solver<M, S>(table_dev, count, prm, G, nteams, smem, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "solver launch");
-    (void)maxn;
-    (void)maxwork;
+    prm.queue = nullptr;
+    return prm;
+}
+
+int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+    return sms > 0 ? sms : 148;
+}
+
+template <class M, class S>
+int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_t ws_bytes, ff_result* res,
+        void* const* w_out, void* const* yA_out, void* const* yD_out, cudaStream_t stream) {
+    std::vector<Sizes> sz(count);
+    size_t need = table_bytes<M, S>(count);
+    for (int t = 0; t < count; ++t) {
+        sz[t] = sizes_of(probs[t]);
+        if (!supported(sz[t], probs[t].omega_diag, o.precision)) return FF_ERR_UNSUPPORTED;
+        need += inst_bytes(sz[t], probs[t].omega_diag, o.precision);
+    }
+    if (!ws || ((uintptr_t)ws % kAlign) != 0 || ws_bytes < need) return FF_ERR_WORKSPACE;
+    // cluster size per instance, then groups of equal cluster size (largest
+    // first); inside a group the largest work comes first in the queue
+    std::vector<int> G;
+    if (o.cluster_size > 0) G.assign(count, o.cluster_size);
+    else choose_clusters(sz, o.cta_work, sm_count(), G);
+    auto work = [&](int t) { return (long long)sz[t].n * sz[t].P * (sz[t].k + sz[t].m + 16); };
+    std::vector<int> order(count);
+    for (int t = 0; t < count; ++t) order[t] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (G[a] != G[b]) return G[a] > G[b];
+        return work(a) > work(b);
+    });
+    unsigned char* base = (unsigned char*)ws;
+    // table region: count Inst records, count ff_problem records (slot order), queue counters
+    Inst<M, S>* table_dev = (Inst<M, S>*)base;
+    ff_problem* probs_dev = (ff_problem*)(base + a256((size_t)count * sizeof(Inst<M, S>)));
+    int* queue_dev = (int*)(base + a256((size_t)count * sizeof(Inst<M, S>)) + a256((size_t)count * sizeof(ff_problem)));
+    unsigned char* cur = base + table_bytes<M, S>(count);
+    std::vector<unsigned char> staging(table_bytes<M, S>(count) - kQueueBytes);
+    Inst<M, S>* table = (Inst<M, S>*)staging.data();
+    ff_problem* pslot = (ff_problem*)(staging.data() + a256((size_t)count * sizeof(Inst<M, S>)));
+    long long maxel = 1;
+    for (int slot = 0; slot < count; ++slot) {
+        int t = order[slot];
+        table[slot] = carve<M, S>(probs[t], sz[t], cur, w_out[t], yA_out ? yA_out[t] : nullptr,
+                                  yD_out ? yD_out[t] : nullptr, res + t);
+        pslot[slot] = probs[t];
+        maxel = std::max(maxel, (long long)sz[t].np * std::max(std::max(sz[t].k, sz[t].m), sz[t].P + sz[t].R));
+    }
+    // groups: [first slot, end slot) of equal G, at most kMaxGroups
+    int gfirst[kMaxGroups + 1], gG[kMaxGroups], ng = 0;
+    for (int slot = 0; slot < count; ++slot) {
+        const int g = G[order[slot]];
+        if (ng == 0 || gG[ng - 1] != g) {
+            if (ng == kMaxGroups) return FF_ERR_INVALID_ARG;
+            gfirst[ng] = slot;
+            gG[ng] = g;
+            ++ng;
+        }
+    }
+    gfirst[ng] = count;
+    // shared memory and teams of every group (a group whose cluster cannot be
+    // resident falls back to half the cluster size)
+    size_t gsmem[kMaxGroups];
+    int gteams[kMaxGroups];
+    cudaError_t e = cudaSuccess;
+    for (int gi = 0; gi < ng; ++gi) {
+        size_t smem = 0;
+        for (int slot = gfirst[gi]; slot < gfirst[gi + 1]; ++slot) {
+            const int t = order[slot];
+            smem = std::max(smem, solver_smem_bytes(sz[t].P, sz[t].k, sz[t].m, probs[t].omega_diag,
+                                                    matvec_elem(o.precision)));
+        }
+        int maxc = 0;
+        for (;;) {
+            e = max_teams<M, S>(gG[gi], smem, &maxc);
+            if (e != cudaSuccess) return cuda_fail(e, "occupancy query of the solver kernel");
+            if (maxc >= 1 || gG[gi] == 1 || o.cluster_size > 0) break;
+            gG[gi] /= 2;
+        }
+        if (maxc < 1) return FF_ERR_UNSUPPORTED;
+        int nteams = std::min(gfirst[gi + 1] - gfirst[gi], maxc);
+        if (o.max_teams > 0) nteams = std::min(nteams, o.max_teams);
+        gsmem[gi] = smem;
+        gteams[gi] = nteams;
+    }
+    if (o.reuse_workspace != 1 && o.reuse_workspace != 2) {
+        e = cudaMemcpyAsync(base, staging.data(), staging.size(), cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "copy of the instance table");
+    }
+    if (o.reuse_workspace != 1) {
+        const int bx = (int)std::min<long long>(64, (maxel + 255) / 256);
+        repack_batch_kernel<M, S><<<dim3((unsigned)bx, (unsigned)count), 256, 0, stream>>>(probs_dev, table_dev);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "repack launch");
+    }
+    e = cudaMemsetAsync(queue_dev, 0, kQueueBytes, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    Params prm = make_params(o);
+    if (ng == 1) {
+        prm.queue = queue_dev;
+        e = launch_solver<M, S>(table_dev, count, prm, gG[0], gteams[0], gsmem[0], stream);
+        if (e != cudaSuccess) return cuda_fail(e, "solver launch");
+        return FF_OK;
+    }
+    // several groups: one launch each on its own side stream, forked from and
+    // joined back into the caller's stream
+    std::lock_guard<std::mutex> lock(g_streams_mu);
+    DeviceStreams* ds = nullptr;
+    int rc = device_streams(&ds);
+    if (rc != FF_OK) return rc;
+    e = cudaEventRecord(ds->fork, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "fork event");
+    for (int gi = 0; gi < ng; ++gi) {
+        // group 0 has the largest clusters and takes the highest-priority stream
+        cudaStream_t sst = ds->side[gi];
+        e = cudaStreamWaitEvent(sst, ds->fork, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "fork wait");
+        prm.queue = queue_dev + gi;
+        e = launch_solver<M, S>(table_dev + gfirst[gi], gfirst[gi + 1] - gfirst[gi], prm, gG[gi], gteams[gi],
+                                gsmem[gi], sst);
+        if (e != cudaSuccess) return cuda_fail(e, "solver launch");
+        e = cudaEventRecord(ds->join[gi], sst);
+        if (e != cudaSuccess) return cuda_fail(e, "join event");
+        e = cudaStreamWaitEvent(stream, ds->join[gi], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "join wait");
+    }
     return FF_OK;
 }
 
@@ -414,7 +550,7 @@ int run_single_static(const ff_problem& p, const ff_options& o, ff_result* res, 
     if (!supported(sz, p.omega_diag, o.precision)) return FF_ERR_UNSUPPORTED;
     constexpr size_t kInstBytes = c_a256(sizeof(Inst<M, S>));
     constexpr size_t kStage = kInstBytes + c_a256(sizeof(ff_problem));
-    const size_t need = kStage + inst_bytes(sz, p.omega_diag, o.precision);
+    const size_t need = kStage + kQueueBytes + inst_bytes(sz, p.omega_diag, o.precision);
     if (need > (size_t)FF_STATIC_WORKSPACE_BYTES) {
         snprintf(g_last_error, sizeof(g_last_error),
                  "problem needs %zu bytes of workspace; the static workspace holds %zu", need,
@@ -425,7 +561,7 @@ int run_single_static(const ff_problem& p, const ff_options& o, ff_result* res, 
     if (!base) return FF_ERR_CUDA;
     alignas(16) unsigned char staging[kStage];
     memset(staging, 0, sizeof(staging));
-    unsigned char* cur = base + kStage;
+    unsigned char* cur = base + kStage + kQueueBytes;
     Inst<M, S> inst = carve<M, S>(p, sz, cur, w_out, yA_out, yD_out, res);
     memcpy(staging, &inst, sizeof(inst));
     memcpy(staging + kInstBytes, &p, sizeof(ff_problem));
@@ -446,17 +582,11 @@ int run_single_static(const ff_problem& p, const ff_options& o, ff_result* res, 
     e = max_teams<M, S>(G, smem, &maxc);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query of the solver kernel");
     if (maxc < 1) return FF_ERR_UNSUPPORTED;
-    Params prm;
-    prm.tol = o.tol;
-    prm.max_iter = o.max_iter;
-    prm.time_limit_ns = o.time_limit * 1e9;
-    prm.check_every = o.check_every;
-    prm.rho = o.reflection;
-    prm.beta_suff = o.restart_sufficient;
-    prm.beta_nec = o.restart_necessary;
-    prm.step_fraction = o.step_fraction;
-    prm.beta = o.beta;
-    prm.power_iters = 60;
+    int* queue_dev = (int*)(base + kStage);
+    e = cudaMemsetAsync(queue_dev, 0, kQueueBytes, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+    Params prm = make_params(o);
+    prm.queue = queue_dev;
     e = launch_solver<M, S>(table_dev, 1, prm, G, 1, smem, stream);
     if (e != cudaSuccess) return cuda_fail(e, "solver launch");
     return FF_OK;
@@ -519,6 +649,31 @@ int ff_solve_multi(const ff_problem* p, const ff_options* o, void* ws, size_t ws
 int ff_solve_batch(const ff_problem* probs, int count, const ff_options* o, void* ws, size_t ws_bytes,
                    ff_result* result_dev, void* const* w_out, void* stream) {
     return ff::dispatch(probs, count, o, ws, ws_bytes, result_dev, w_out, nullptr, nullptr, stream);
+}
+
+int ff_batch_plan(const ff_problem* probs, int count, const ff_options* o_in, int32_t* cluster_out,
+                  int32_t* launches_out) {
+    if (count < 1 || !probs) return FF_ERR_INVALID_ARG;
+    ff_options o;
+    if (o_in) o = *o_in; else ff::fill_defaults(&o);
+    if (!ff::valid_options(o)) return FF_ERR_INVALID_ARG;
+    std::vector<ff::Sizes> sz(count);
+    for (int t = 0; t < count; ++t) {
+        if (!ff::valid_problem(&probs[t])) return FF_ERR_INVALID_ARG;
+        sz[t] = ff::sizes_of(probs[t]);
+    }
+    std::vector<int> G;
+    if (o.cluster_size > 0) G.assign(count, o.cluster_size);
+    else ff::choose_clusters(sz, o.cta_work, ff::sm_count(), G);
+    int distinct[16] = {0}, nd = 0;
+    for (int t = 0; t < count; ++t) {
+        if (cluster_out) cluster_out[t] = G[t];
+        bool seen = false;
+        for (int i = 0; i < nd; ++i) seen = seen || distinct[i] == G[t];
+        if (!seen) distinct[nd++] = G[t];
+    }
+    if (launches_out) *launches_out = nd;
+    return FF_OK;
 }
 
 int ff_solve_single_static(const ff_problem* p, const ff_options* o, ff_result* result_dev, void* w_out,

@@ -61,6 +61,8 @@ struct Params {
     double step_fraction;
     double beta;
     int power_iters;
+    int* queue;          // device counter of the next instance (zero at launch); teams take
+                         // instances from it in table order
 };
 
 // Shared-memory bytes the solver kernel needs for these sizes.

@@ -1,6 +1,7 @@
 // Persistent "team" kernel: one thread-block cluster of G CTAs solves one
 // portfolio instance at a time (single-period model, Sec. 2.1, or
-// multi-period model, Sec. 2.2) and then takes the next instance of the batch.
+// multi-period model, Sec. 2.2) and then takes the next instance of the batch
+// from a device queue (largest first, so the tail is short).
 //
 // Method: restarted, reflected Halpern iteration of the Condat-Vu primal-dual
 // splitting (the paper only states that its first-order method stops on a
@@ -603,10 +604,16 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
     cg::cluster_group cl = cg::this_cluster();
     const int G = (int)cl.num_blocks();
     const int g = (int)cl.block_rank();
-    const int team = blockIdx.x / G;
-    const int nteams = gridDim.x / G;
+    __shared__ int next_s;
 
-    for (int inst = team; inst < count; inst += nteams) {
+    for (;;) {
+        // the team's rank-0 thread takes the next instance from the queue and
+        // the other ranks read it from rank 0's shared memory
+        if (g == 0 && threadIdx.x == 0) next_s = atomicAdd(prm.queue, 1);
+        cl.sync();
+        const int inst = *cl.map_shared_rank(&next_s, 0);
+        cl.sync();
+        if (inst >= count) break;
         Ctx<M, S> c;
         c.I = insts[inst];
         c.n = c.I.n; c.k = c.I.k; c.m = c.I.m; c.P = c.I.P; c.R = c.I.R; c.np = c.I.np;

@@ -62,3 +62,21 @@ def test_workspace_size_grows_with_n(lib):
         return _lib.ff_workspace_size(C.byref(p), 1, o)
 
     assert 0 < ws(100) < ws(1000) < ws(1000, T=5)
+
+
+def test_batch_plan_groups_by_cluster_size(lib):
+    """The host-only plan gives small single-period instances one CTA and
+    spreads large multi-period ones over clusters (no GPU needed)."""
+    import numpy as np
+    from paper_2604_22625_gb300 import api, synthetic as S
+    probs = [S.make_single(n, 20, i) for i, n in enumerate([600, 3000, 7000] * 40)]
+    probs += [S.make_multi(30, 3500, 20, 99)]
+    flat, lay = api.pack(probs, np.float32)
+    st = (_lib.ff_problem * len(probs))(*[api._struct(p, e, 1 << 20, 4, _lib.FF_F32) for p, e in zip(probs, lay)])
+    o = _lib.default_options(precision=_lib.FF_PREC_BF16)
+    cl, nl = _lib.ff_batch_plan(st, len(probs), o)
+    assert cl[:120] == [1] * 120
+    assert cl[-1] == 16 and nl == 2          # 29 * 3500 asset-periods > 8 * 8192
+    o.cluster_size = 4
+    cl, nl = _lib.ff_batch_plan(st, len(probs), o)
+    assert set(cl) == {4} and nl == 1

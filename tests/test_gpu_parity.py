@@ -119,3 +119,39 @@ def test_batch_bf16_mixed(api):
         s.info = info
         s.yA = None
         _compare(p, s)
+
+
+def test_batch_graph_replay_matches_direct_call(api):
+    """The captured CUDA graph (repack + every group's persistent launch)
+    reproduces the direct call bit for bit, and re-solves after the inputs
+    change in place."""
+    import torch
+    probs = [S.make_single(n, 40, 300 + i) for i, n in enumerate([900, 2600, 150])]
+    probs += [S.make_multi(6, 500, 40, 310)]
+    br = api.BatchRunner(probs, precision="bf16")
+    br.run()
+    torch.cuda.synchronize()
+    w_direct = [w.copy() for w in br.portfolios()]
+    br.capture()
+    br.w_dev.zero_()
+    br.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(w_direct, br.portfolios()):
+        assert np.array_equal(a, b)
+    infos = br.results()
+    assert all(i["status_name"] == "converged" for i in infos)
+    # new alpha values written into the packed device buffer are picked up by the replay
+    off, size = br.layout[0]["alpha"]
+    br.dev_in[off:off + size] *= 0.5
+    br.replay()
+    torch.cuda.synchronize()
+
+    class _Sol:
+        pass
+    sol = _Sol()
+    sol.x = np.asarray(br.portfolios()[0]).reshape(1, -1)
+    sol.info = br.results()[0]
+    sol.yA = None
+    pr = probs[0].with_F_rounded_bf16()
+    pr.alpha = pr.alpha * 0.5          # exact: alpha is FP32-rounded
+    _compare(pr, sol)
