@@ -212,7 +212,8 @@ int ff_solve_single_static(const ff_problem* p, const ff_options* o, ff_result* 
  * device work; it reads the SM count of the current device when one is
  * present): cluster_out (HOST, count entries, may be NULL) receives each
  * instance's CTAs per instance, launches_out (may be NULL) the number of
- * persistent solver launches (one per distinct cluster size).  A cluster
+ * persistent solver launches (one per distinct cluster size and kind,
+ * single- or multi-period).  A cluster
  * size that cannot be resident on the device is halved at solve time. */
 int ff_batch_plan(const ff_problem* probs, int count, const ff_options* o, int32_t* cluster_out,
                   int32_t* launches_out);

@@ -75,7 +75,7 @@ size_t inst_bytes(const Sizes& s, int omega_diag, int precision) {
 
 // instance table + problem copies at the start of the workspace
 constexpr size_t kQueueBytes = 256;   // per-group instance counters of the device queue
-constexpr int kMaxGroups = 5;         // cluster sizes 1, 2, 4, 8, 16
+constexpr int kMaxGroups = 10;        // cluster sizes 1, 2, 4, 8, 16, single- or multi-period
 
 template <class M, class S>
 size_t table_bytes(int count) {
@@ -389,6 +389,7 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
     for (int t = 0; t < count; ++t) order[t] = t;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
         if (G[a] != G[b]) return G[a] > G[b];
+        if (sz[a].multi != sz[b].multi) return sz[a].multi > sz[b].multi;
         return work(a) > work(b);
     });
     unsigned char* base = (unsigned char*)ws;
@@ -408,14 +409,18 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
         pslot[slot] = probs[t];
         maxel = std::max(maxel, (long long)sz[t].np * std::max(std::max(sz[t].k, sz[t].m), sz[t].P + sz[t].R));
     }
-    // groups: [first slot, end slot) of equal G, at most kMaxGroups
+    // groups: [first slot, end slot) of equal G and kind (single- or
+    // multi-period), at most kMaxGroups
     int gfirst[kMaxGroups + 1], gG[kMaxGroups], ng = 0;
+    bool gsingle[kMaxGroups];
     for (int slot = 0; slot < count; ++slot) {
         const int g = G[order[slot]];
-        if (ng == 0 || gG[ng - 1] != g) {
+        const bool single = !sz[order[slot]].multi;
+        if (ng == 0 || gG[ng - 1] != g || gsingle[ng - 1] != single) {
             if (ng == kMaxGroups) return FF_ERR_INVALID_ARG;
             gfirst[ng] = slot;
             gG[ng] = g;
+            gsingle[ng] = single;
             ++ng;
         }
     }
@@ -434,7 +439,7 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
         }
         int maxc = 0;
         for (;;) {
-            e = max_teams<M, S>(gG[gi], smem, &maxc);
+            e = max_teams<M, S>(gG[gi], smem, gsingle[gi], &maxc);
             if (e != cudaSuccess) return cuda_fail(e, "occupancy query of the solver kernel");
             if (maxc >= 1 || gG[gi] == 1 || o.cluster_size > 0) break;
             gG[gi] /= 2;
@@ -460,7 +465,7 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
     Params prm = make_params(o);
     if (ng == 1) {
         prm.queue = queue_dev;
-        e = launch_solver<M, S>(table_dev, count, prm, gG[0], gteams[0], gsmem[0], stream);
+        e = launch_solver<M, S>(table_dev, count, prm, gG[0], gteams[0], gsmem[0], gsingle[0], stream);
         if (e != cudaSuccess) return cuda_fail(e, "solver launch");
         return FF_OK;
     }
@@ -479,7 +484,7 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
         if (e != cudaSuccess) return cuda_fail(e, "fork wait");
         prm.queue = queue_dev + gi;
         e = launch_solver<M, S>(table_dev + gfirst[gi], gfirst[gi + 1] - gfirst[gi], prm, gG[gi], gteams[gi],
-                                gsmem[gi], sst);
+                                gsmem[gi], gsingle[gi], sst);
         if (e != cudaSuccess) return cuda_fail(e, "solver launch");
         e = cudaEventRecord(ds->join[gi], sst);
         if (e != cudaSuccess) return cuda_fail(e, "join event");
@@ -579,7 +584,7 @@ int run_single_static(const ff_problem& p, const ff_options& o, ff_result* res, 
     const size_t smem = solver_smem_bytes(sz.P, sz.k, sz.m, p.omega_diag, matvec_elem(o.precision));
     const int G = o.cluster_size > 0 ? o.cluster_size : auto_cluster(sz, 1);
     int maxc = 0;
-    e = max_teams<M, S>(G, smem, &maxc);
+    e = max_teams<M, S>(G, smem, true, &maxc);
     if (e != cudaSuccess) return cuda_fail(e, "occupancy query of the solver kernel");
     if (maxc < 1) return FF_ERR_UNSUPPORTED;
     int* queue_dev = (int*)(base + kStage);
@@ -587,7 +592,7 @@ int run_single_static(const ff_problem& p, const ff_options& o, ff_result* res, 
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
     Params prm = make_params(o);
     prm.queue = queue_dev;
-    e = launch_solver<M, S>(table_dev, 1, prm, G, 1, smem, stream);
+    e = launch_solver<M, S>(table_dev, 1, prm, G, 1, smem, true, stream);
     if (e != cudaSuccess) return cuda_fail(e, "solver launch");
     return FF_OK;
 }
@@ -665,12 +670,13 @@ int ff_batch_plan(const ff_problem* probs, int count, const ff_options* o_in, in
     std::vector<int> G;
     if (o.cluster_size > 0) G.assign(count, o.cluster_size);
     else ff::choose_clusters(sz, o.cta_work, ff::sm_count(), G);
-    int distinct[16] = {0}, nd = 0;
+    int distinct[32] = {0}, nd = 0;
     for (int t = 0; t < count; ++t) {
         if (cluster_out) cluster_out[t] = G[t];
+        const int key = 2 * G[t] + (sz[t].multi ? 1 : 0);
         bool seen = false;
-        for (int i = 0; i < nd; ++i) seen = seen || distinct[i] == G[t];
-        if (!seen) distinct[nd++] = G[t];
+        for (int i = 0; i < nd; ++i) seen = seen || distinct[i] == key;
+        if (!seen) distinct[nd++] = key;
     }
     if (launches_out) *launches_out = nd;
     return FF_OK;

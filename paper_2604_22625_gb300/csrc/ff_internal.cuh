@@ -15,6 +15,7 @@ constexpr int kPC = 8;                 // periods processed together in a matvec
 constexpr int kCand = 8;               // threshold candidates per period and search round
 constexpr int kMaxRounds = 16;         // threshold search rounds per projection
 constexpr int kMaxCluster = 16;
+constexpr int kSingleCtasPerSm = 1;    // resident CTAs per SM the single-period variant is built for
 
 // One instance as the solver kernel sees it (device memory).  All per-asset
 // arrays have row stride np (n rounded up to a multiple of 32).  Panels are
@@ -69,12 +70,13 @@ struct Params {
 size_t solver_smem_bytes(int P, int k, int m, int omega_diag, size_t matvec_size);
 
 // Launch the team kernel over `count` instances (insts is a device array).
-// G = CTAs per instance (cluster size), nteams = concurrent teams.
+// G = CTAs per instance (cluster size), nteams = concurrent teams; single =
+// every instance is single-period (the variant built for P = 1).
 template <class M, class S>
 cudaError_t launch_solver(const Inst<M, S>* insts, int count, const Params& prm, int G, int nteams,
-                          size_t smem, cudaStream_t stream);
+                          size_t smem, bool single, cudaStream_t stream);
 
 template <class M, class S>
-cudaError_t max_teams(int G, size_t smem, int* out);
+cudaError_t max_teams(int G, size_t smem, bool single, int* out);
 
 }  // namespace ff

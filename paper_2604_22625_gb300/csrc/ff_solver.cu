@@ -60,7 +60,7 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 
 __host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_diag, size_t ms) {
     Layout L;
-    L.vlen = kPC * (2 * m + 2 * k);
+    L.vlen = (P < kPC ? P : kPC) * (2 * m + 2 * k);
     const int slots = (kWarps * P * kCand + 1) / 2;   // 4-byte threshold slots in 8-byte units
     if (L.vlen < slots) L.vlen = slots;
     int s1 = P * kCand * 2, s2 = P + 48;
@@ -74,9 +74,10 @@ __host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_dia
     L.wred = take((size_t)kWarps * 32 * 8);
     L.stage = take((size_t)2048 * ms);              // 4 vectors x PCT periods x 512/PCT assets
     L.yA = take((size_t)P * m * 8);
-    L.yAb = take((size_t)((P + kPC - 1) / kPC * kPC) * m * 8);
+    // whole chunks for the expand pass weights (a single period needs no padding)
+    const int Pr = P <= 1 ? 1 : (P + kPC - 1) / kPC * kPC;
+    L.yAb = take((size_t)Pr * m * 8);
     L.ax = take((size_t)P * m * 8);
-    const int Pr = (P + kPC - 1) / kPC * kPC;        // whole chunks for the expand pass weights
     L.u = take((size_t)P * k * 8);
     L.ub = take((size_t)Pr * k * 8);
     L.om = take((size_t)Pr * k * ms);
@@ -384,13 +385,19 @@ __device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, c
     __syncthreads();
 }
 
-template <class M, class S>
+// PCMAX = 1: the kernel variant for single-period instances (only the
+// one-period code is instantiated, which keeps its register count low)
+template <int PCMAX, class M, class S>
 __device__ void reduce_chunk(Ctx<M, S>& c, int p0, int pc, const double* a0, const double* a1, const double* f0,
                              const double* f1, bool subcen) {
-    if (pc <= 1) reduce_chunk_t<1>(c, p0, pc, a0, a1, f0, f1, subcen);
-    else if (pc <= 2) reduce_chunk_t<2>(c, p0, pc, a0, a1, f0, f1, subcen);
-    else if (pc <= 4) reduce_chunk_t<4>(c, p0, pc, a0, a1, f0, f1, subcen);
-    else reduce_chunk_t<8>(c, p0, pc, a0, a1, f0, f1, subcen);
+    if constexpr (PCMAX == 1) {
+        reduce_chunk_t<1>(c, p0, pc, a0, a1, f0, f1, subcen);
+    } else {
+        if (pc <= 1) reduce_chunk_t<1>(c, p0, pc, a0, a1, f0, f1, subcen);
+        else if (pc <= 2) reduce_chunk_t<2>(c, p0, pc, a0, a1, f0, f1, subcen);
+        else if (pc <= 4) reduce_chunk_t<4>(c, p0, pc, a0, a1, f0, f1, subcen);
+        else reduce_chunk_t<8>(c, p0, pc, a0, a1, f0, f1, subcen);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -444,15 +451,19 @@ __device__ void expand_chunk(Ctx<M, S>& c, int i, int p0, int pc, const W* wF, c
 
 // The weight vectors must have PCT rows readable past Pv: callers size the
 // replicated arrays for whole chunks (rows beyond Pv hold finite values).
-template <class A, class M, class S, class W, class Epi>
+template <class A, int PCMAX, class M, class S, class W, class Epi>
 __device__ void expand_pass(Ctx<M, S>& c, int Pv, const W* wF, const W* wA, Epi epi) {
     for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
-        for (int p0 = 0; p0 < Pv; p0 += kPC) {
-            const int pc = min(kPC, Pv - p0);
-            if (pc <= 1) expand_chunk<1, A>(c, i, p0, pc, wF, wA, epi);
-            else if (pc <= 2) expand_chunk<2, A>(c, i, p0, pc, wF, wA, epi);
-            else if (pc <= 4) expand_chunk<4, A>(c, i, p0, pc, wF, wA, epi);
-            else expand_chunk<8, A>(c, i, p0, pc, wF, wA, epi);
+        if constexpr (PCMAX == 1) {
+            expand_chunk<1, A>(c, i, 0, 1, wF, wA, epi);
+        } else {
+            for (int p0 = 0; p0 < Pv; p0 += kPC) {
+                const int pc = min(kPC, Pv - p0);
+                if (pc <= 1) expand_chunk<1, A>(c, i, p0, pc, wF, wA, epi);
+                else if (pc <= 2) expand_chunk<2, A>(c, i, p0, pc, wF, wA, epi);
+                else if (pc <= 4) expand_chunk<4, A>(c, i, p0, pc, wF, wA, epi);
+                else expand_chunk<8, A>(c, i, p0, pc, wF, wA, epi);
+            }
         }
     }
 }
@@ -597,8 +608,8 @@ __device__ void apply_omega_m(Ctx<M, S>& c, const double* uin, M* out, int Pv) {
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
-template <class M, class S>
-__global__ void __launch_bounds__(kThreads, 1)
+template <class M, class S, int PCMAX>
+__global__ void __launch_bounds__(kThreads, PCMAX == 1 ? kSingleCtasPerSm : 1)
 team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
     extern __shared__ __align__(16) unsigned char smem[];
     cg::cluster_group cl = cg::this_cluster();
@@ -616,7 +627,9 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         if (inst >= count) break;
         Ctx<M, S> c;
         c.I = insts[inst];
-        c.n = c.I.n; c.k = c.I.k; c.m = c.I.m; c.P = c.I.P; c.R = c.I.R; c.np = c.I.np;
+        c.n = c.I.n; c.k = c.I.k; c.m = c.I.m; c.np = c.I.np;
+        c.P = PCMAX == 1 ? 1 : c.I.P;
+        c.R = PCMAX == 1 ? 1 : c.I.R;
         c.G = G; c.g = g;
         c.tid = threadIdx.x; c.lane = threadIdx.x & 31; c.warp = threadIdx.x >> 5;
         c.i0 = (int)(((long long)c.n * g) / G);
@@ -674,14 +687,14 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             }
             __syncthreads();
             for (int it = 0; it < prm.power_iters; ++it) {
-                reduce_chunk(c, 0, 1, v2, (const double*)nullptr, v1, (const double*)nullptr, false);
+                reduce_chunk<PCMAX>(c, 0, 1, v2, (const double*)nullptr, v1, (const double*)nullptr, false);
                 team_reduce<false>(cl, c.vpart, c.vout, Lr, G, g);
                 for (int e = c.tid; e < k; e += kThreads) c.u[e] = c.vout[2 * m + e];
                 for (int e = c.tid; e < m; e += kThreads) c.yAm[e] = (M)c.vout[e];
                 __syncthreads();
                 apply_omega_m(c, c.u, c.om, 1);
                 double nrm[2] = {0, 0};
-                expand_pass<M>(c, 1, c.om, c.yAm, [&](int i, int p, double aF, double aA) {
+                expand_pass<M, PCMAX>(c, 1, c.om, c.yAm, [&](int i, int p, double aF, double aA) {
                     const double w1 = aF + c.I.Dmax[i] * v1[i];
                     nrm[0] += w1 * w1;
                     nrm[1] += aA * aA;
@@ -743,7 +756,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         // u = F^T (x - c), ax = A x
         for (int p0 = 0; p0 < P; p0 += kPC) {
             const int pc = min(kPC, P - p0);
-            reduce_chunk(c, p0, pc, c.I.x, (const double*)nullptr, c.I.x, (const double*)nullptr, true);
+            reduce_chunk<PCMAX>(c, p0, pc, c.I.x, (const double*)nullptr, c.I.x, (const double*)nullptr, true);
             team_reduce<false>(cl, c.vpart, c.vout, pc * Lr, G, g);
             for (int e = c.tid; e < pc * m; e += kThreads) c.ax[p0 * m + e] = c.vout[(e / m) * Lr + e % m];
             for (int e = c.tid; e < pc * k; e += kThreads)
@@ -779,7 +792,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                 const double* yD = c.I.yD;
                 double* v = c.I.v;
                 const M kapm = (M)kap;
-                expand_pass<M>(c, P, c.om, c.yAm, [&](int i, int p, double aF, double aA) {
+                expand_pass<M, PCMAX>(c, P, c.om, c.yAm, [&](int i, int p, double aF, double aA) {
                     // gradient and K^T y in M; the state update in FP64
                     const size_t o = (size_t)p * np + i;
                     const double xv = x[o];
@@ -839,7 +852,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             double rA = 0, pin = 0, nAx = 0, nCl = 0;
             for (int p0 = 0; p0 < P; p0 += kPC) {
                 const int pc = min(kPC, P - p0);
-                reduce_chunk(c, p0, pc, c.I.xb, c.I.xn, c.I.xn, check ? c.I.xb : (const double*)nullptr, true);
+                reduce_chunk<PCMAX>(c, p0, pc, c.I.xb, c.I.xn, c.I.xn, check ? c.I.xb : (const double*)nullptr, true);
                 team_reduce<false>(cl, c.vpart, c.vout, pc * Lr, G, g);
                 for (int e = c.tid; e < pc * m; e += kThreads) {
                     const int q = e / m, jj = e % m;
@@ -920,7 +933,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                 const double* xb = c.I.xb;
                 const double* ydb = c.I.yDb;
                 double* qv = c.I.v;
-                expand_pass<double>(c, P, c.ub, c.yAb, [&](int i, int p, double aF, double aA) {
+                expand_pass<double, PCMAX>(c, P, c.ub, c.yAb, [&](int i, int p, double aF, double aA) {
                     const size_t o = (size_t)p * np + i;
                     const double xv = xb[o];
                     const double dx = xv - c.I.cen[i];
@@ -1079,61 +1092,67 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
     }
 }
 
-template <class M, class S>
+template <class M, class S, int PCMAX>
 static cudaError_t prepare(int G, size_t smem) {
-    auto kern = team_kernel<M, S>;
+    auto kern = team_kernel<M, S, PCMAX>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (G > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     return e;
 }
 
-template <class M, class S>
-cudaError_t launch_solver(const Inst<M, S>* insts, int count, const Params& prm, int G, int nteams, size_t smem,
-                          cudaStream_t stream) {
-    cudaError_t e = prepare<M, S>(G, smem);
-    if (e != cudaSuccess) return e;
+static cudaLaunchConfig_t team_config(int G, int nteams, size_t smem, cudaStream_t stream, cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(G * nteams), 1, 1);
     cfg.blockDim = dim3(kThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)G;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, team_kernel<M, S>, insts, count, prm);
+    return cfg;
 }
 
 template <class M, class S>
-cudaError_t max_teams(int G, size_t smem, int* out) {
-    cudaError_t e = prepare<M, S>(G, smem);
-    if (e != cudaSuccess) return e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)G, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
+cudaError_t launch_solver(const Inst<M, S>* insts, int count, const Params& prm, int G, int nteams, size_t smem,
+                          bool single, cudaStream_t stream) {
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)G;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(out, team_kernel<M, S>, &cfg);
+    cudaLaunchConfig_t cfg = team_config(G, nteams, smem, stream, attr);
+    if (single) {
+        cudaError_t e = prepare<M, S, 1>(G, smem);
+        if (e != cudaSuccess) return e;
+        return cudaLaunchKernelEx(&cfg, team_kernel<M, S, 1>, insts, count, prm);
+    }
+    cudaError_t e = prepare<M, S, kPC>(G, smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, team_kernel<M, S, kPC>, insts, count, prm);
+}
+
+template <class M, class S>
+cudaError_t max_teams(int G, size_t smem, bool single, int* out) {
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = team_config(G, 1, smem, 0, attr);
+    if (single) {
+        cudaError_t e = prepare<M, S, 1>(G, smem);
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveClusters(out, team_kernel<M, S, 1>, &cfg);
+    }
+    cudaError_t e = prepare<M, S, kPC>(G, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveClusters(out, team_kernel<M, S, kPC>, &cfg);
 }
 
 template cudaError_t launch_solver<double, double>(const Inst<double, double>*, int, const Params&, int, int,
-                                                   size_t, cudaStream_t);
+                                                   size_t, bool, cudaStream_t);
 template cudaError_t launch_solver<float, float>(const Inst<float, float>*, int, const Params&, int, int, size_t,
-                                                 cudaStream_t);
+                                                 bool, cudaStream_t);
 template cudaError_t launch_solver<float, __nv_bfloat16>(const Inst<float, __nv_bfloat16>*, int, const Params&,
-                                                         int, int, size_t, cudaStream_t);
-template cudaError_t max_teams<double, double>(int, size_t, int*);
-template cudaError_t max_teams<float, float>(int, size_t, int*);
-template cudaError_t max_teams<float, __nv_bfloat16>(int, size_t, int*);
+                                                         int, int, size_t, bool, cudaStream_t);
+template cudaError_t max_teams<double, double>(int, size_t, bool, int*);
+template cudaError_t max_teams<float, float>(int, size_t, bool, int*);
+template cudaError_t max_teams<float, __nv_bfloat16>(int, size_t, bool, int*);
 
 }  // namespace ff
