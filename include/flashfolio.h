@@ -58,6 +58,7 @@ extern "C" {
 #define FF_MAX_ITER            1   /* iteration limit reached */
 #define FF_TIME_LIMIT          2   /* device clock passed options.time_limit */
 #define FF_NUMERICAL           3   /* NaN/Inf met in the iteration */
+#define FF_STALLED             4   /* a bounded wait for a panel tile copy expired */
 
 /* element types */
 #define FF_F64                 0
@@ -126,11 +127,14 @@ typedef struct ff_options {
                                    n * P / G <= cta_work); default 8192.  Instances of equal G
                                    form one persistent launch; the launches run concurrently
                                    on library-owned streams forked from `stream`. */
+    double  restart_artificial; /* also restart once the iterations since the last restart
+                                   reach this share of all iterations so far (0 = off);
+                                   default 0.36 */
 } ff_options;
 
 /* Per-instance outcome, written to DEVICE memory by the solve calls. */
 typedef struct ff_result {
-    int32_t status;             /* FF_CONVERGED, FF_MAX_ITER, FF_TIME_LIMIT, FF_NUMERICAL */
+    int32_t status;             /* FF_CONVERGED, FF_MAX_ITER, FF_TIME_LIMIT, FF_NUMERICAL, FF_STALLED */
     int32_t restarts;
     int64_t iterations;
     double  rel_kkt;            /* max(r_primal, r_dual, r_gap) at the returned point */

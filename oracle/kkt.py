@@ -15,7 +15,11 @@ project reports instead:
 
     r_p   = ||Ax - clip(Ax, L, U)|| / (||Ax|| + ||clip(Ax, L, U)||)
     r_d   = ||x - Proj_B1(x - (grad f(x) + K^T y))|| / (||x|| + ||grad f(x)|| + ||K^T y||)
-    r_gap = |P(x) - D(y; x)| / (|P(x)| + |D(y; x)|)
+    r_gap = |P(x) - D(y; x)| / max(|P(x)| + |D(y; x)|, Phi(x))
+with Phi(x) = sum |alpha_i x_i| + kappa sum_p (x_p - c)^T Sigma_p (x_p - c) + phi(Delta x + b),
+the magnitude of the objective's terms: where the optimal value nearly cancels
+(|P| much smaller than its terms) the gap is measured against the scale at
+which the terms themselves are computed, not against the cancelled value;
 with the weak-duality bound (valid for every x, y)
     D(y; x) = f(x) - <grad f(x), x> - g*(-grad f(x) - K^T y) - h_A*(y_A) - h_D*(y_D),
     g*(v) = sum_p ||v_p||_inf,  h_A*(y) = sum U y^+ - L y^-,
@@ -72,6 +76,16 @@ def dual_bound(sc: Scaled, x: np.ndarray, yA: np.ndarray, yD: np.ndarray) -> flo
     return sc.f(x) - float(np.sum(g * x)) - gstar - hA_conj(sc, yA) - hD_conj(sc, yD)
 
 
+def term_scale(sc: Scaled, x: np.ndarray) -> float:
+    """Phi(x): sum of |alpha_{p,i} x_{p,i}|, the risk terms and the trading cost."""
+    ret = float(np.sum(np.abs(sc.alpha * x)))
+    risk = 0.0
+    for p in range(sc.P):
+        dx = x[p] - sc.center
+        risk += sc.kappa * float(dx @ sc.Sigma_apply(dx, p))
+    return ret + risk + sc.phi(sc.trades(x))
+
+
 def evaluate(sc: Scaled, x, yA, yD) -> KKT:
     """Relative KKT residuals of (x, yA, yD) for the scaled problem ``sc``."""
     x = np.asarray(x, dtype=np.float64).reshape(sc.P, sc.n)
@@ -87,7 +101,7 @@ def evaluate(sc: Scaled, x, yA, yD) -> KKT:
     r_d = np.linalg.norm(x - proj) / (np.linalg.norm(x) + np.linalg.norm(g) + np.linalg.norm(Kty) + TINY)
     P_ = sc.objective(x)
     D_ = dual_bound(sc, x, yA, yD)
-    r_gap = abs(P_ - D_) / (abs(P_) + abs(D_) + TINY)
+    r_gap = abs(P_ - D_) / (max(abs(P_) + abs(D_), term_scale(sc, x)) + TINY)
     return KKT(P_, D_, float(r_p), float(r_d), float(r_gap))
 
 

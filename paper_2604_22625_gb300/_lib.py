@@ -25,6 +25,7 @@ FF_CONVERGED = 0
 FF_MAX_ITER = 1
 FF_TIME_LIMIT = 2
 FF_NUMERICAL = 3
+FF_STALLED = 4
 
 FF_F64 = 0
 FF_F32 = 1
@@ -36,7 +37,7 @@ FF_PREC_BF16 = 2
 FF_STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
 STATUS_NAMES = {FF_CONVERGED: "converged", FF_MAX_ITER: "max_iter", FF_TIME_LIMIT: "time_limit",
-                FF_NUMERICAL: "numerical"}
+                FF_NUMERICAL: "numerical", FF_STALLED: "stalled"}
 
 
 class ff_problem(C.Structure):
@@ -54,7 +55,8 @@ class ff_options(C.Structure):
                 ("precision", C.c_int32), ("check_every", C.c_int32), ("reflection", C.c_double),
                 ("restart_sufficient", C.c_double), ("restart_necessary", C.c_double),
                 ("step_fraction", C.c_double), ("cluster_size", C.c_int32), ("max_teams", C.c_int32),
-                ("beta", C.c_double), ("reuse_workspace", C.c_int32), ("cta_work", C.c_double)]
+                ("beta", C.c_double), ("reuse_workspace", C.c_int32), ("cta_work", C.c_double),
+                ("restart_artificial", C.c_double)]
 
 
 class ff_result(C.Structure):

@@ -34,11 +34,18 @@ int cuda_fail(cudaError_t e, const char* where) {
 
 inline size_t a256(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+inline size_t matvec_elem(int precision) { return precision == FF_PREC_F64 ? 8 : 4; }
+inline size_t panel_elem(int precision) {
+    return precision == FF_PREC_F64 ? 8 : (precision == FF_PREC_F32 ? 4 : 2);
+}
+
 struct Sizes {
     int n, k, m, P, R, np, multi;
+    int omega_diag;
+    Tiling tl;        // panel tiling; tl.CH == 0 when no tiling fits shared memory
 };
 
-inline Sizes sizes_of(const ff_problem& p) {
+inline Sizes sizes_of(const ff_problem& p, int precision) {
     Sizes s;
     s.n = p.n;
     s.k = p.k;
@@ -47,20 +54,29 @@ inline Sizes sizes_of(const ff_problem& p) {
     s.P = s.multi ? p.T - 1 : 1;
     s.R = s.multi ? p.T : 1;
     s.np = (p.n + 31) / 32 * 32;
+    s.omega_diag = p.omega_diag ? 1 : 0;
+    const int CH = (s.P <= 64 && s.k + s.m <= 2 * kThreads)
+                       ? choose_tile(s.P, s.k, s.m, s.omega_diag, matvec_elem(precision), panel_elem(precision))
+                       : 0;
+    s.tl = make_tiling(s.n, s.k, s.m, CH > 0 ? CH : 8);
+    s.tl.CH = CH;
     return s;
 }
 
-inline size_t matvec_elem(int precision) { return precision == FF_PREC_F64 ? 8 : 4; }
-inline size_t panel_elem(int precision) {
-    return precision == FF_PREC_F64 ? 8 : (precision == FF_PREC_F32 ? 4 : 2);
+inline size_t smem_of(const Sizes& s, int precision) {
+    return solver_smem_bytes(s.P, s.k, s.m, s.omega_diag, matvec_elem(precision), s.tl.CH, s.tl.Rp,
+                             panel_elem(precision));
+}
+
+inline size_t panel_bytes(const Sizes& s, int precision) {
+    return (size_t)s.tl.ntile * s.tl.Rp * s.tl.CH * panel_elem(precision);
 }
 
 // bytes of workspace of one instance (excluding the Inst table); state is FP64
 size_t inst_bytes(const Sizes& s, int omega_diag, int precision) {
     const size_t r = 8, pe = panel_elem(precision);
     size_t b = 0;
-    b += a256(2 * (size_t)s.k * s.np * pe);                 // F^T and F
-    b += a256(2 * (size_t)s.m * s.np * pe + 16);            // A and A^T
+    b += 2 * a256(panel_bytes(s, precision));               // PE and PR panel tiles
     b += a256((size_t)(omega_diag ? s.k : s.k * s.k) * r);  // Omega
     b += 2 * a256((size_t)s.P * s.np * r);                  // alpha, D
     b += 4 * a256((size_t)s.np * r);                        // Dmax, w0, cen, alphaT
@@ -104,10 +120,11 @@ bool valid_problem(const ff_problem* p) {
 }
 
 bool supported(const Sizes& s, int omega_diag, int precision) {
+    (void)omega_diag;
+    (void)precision;
     if (s.P > 64) return false;              // per-period flags of the threshold search
     if (s.k + s.m > 2 * kThreads) return false;
-    size_t smem = solver_smem_bytes(s.P, s.k, s.m, omega_diag, matvec_elem(precision));
-    return smem <= 227 * 1024 - 1024;   // static shared memory of the kernel needs the rest
+    return s.tl.CH > 0;                      // a tiling whose layout fits shared memory
 }
 
 void fill_defaults(ff_options* o) {
@@ -123,6 +140,7 @@ void fill_defaults(ff_options* o) {
     o->beta = 0.75;
     o->reuse_workspace = 0;
     o->cta_work = 8192.0;
+    o->restart_artificial = 0.36;
     o->cluster_size = 0;
     o->max_teams = 0;
 }
@@ -142,6 +160,7 @@ bool valid_options(const ff_options& o) {
     if (o.max_teams < 0) return false;
     if (o.reuse_workspace < 0 || o.reuse_workspace > 2) return false;
     if (!(o.cta_work >= 1.0)) return false;
+    if (!(o.restart_artificial >= 0 && o.restart_artificial < 1)) return false;
     return true;
 }
 
@@ -170,21 +189,25 @@ __device__ void repack_one(const ff_problem& p, const Inst<M, S>& I, double lam2
     const In* L = (const In*)p.L;
     const In* U = (const In*)p.U;
     const int n = I.n, k = I.k, m = I.m, P = I.P, R = I.R, np = I.np;
-    S* Ft = (S*)I.Ft;
-    S* Fam = Ft + (size_t)k * np;
-    S* At = (S*)I.At;
-    S* Aam = At + (size_t)m * np;
-    for (size_t e = tid; e < (size_t)np * k; e += nth) {
-        int i = (int)(e / k), j = (int)(e % k);
-        double v = (i < n) ? (double)F[(size_t)i * k + j] : 0.0;
-        Fam[e] = to_s<S>(v);
-        Ft[(size_t)j * np + i] = to_s<S>(v);
-    }
-    for (size_t e = tid; e < (size_t)np * m; e += nth) {
-        int i = (int)(e / m), j = (int)(e % m);
-        double v = (i < n) ? (double)A[(size_t)j * n + i] : 0.0;
-        Aam[e] = to_s<S>(v);
-        At[(size_t)j * np + i] = to_s<S>(v);
+    // panel tiles: PE[t][r][ii] and PR[t][ii][r] for asset i = t CH + ii and
+    // panel row r (F rows 0..k-1, A rows kp..kp+m-1, zero padding elsewhere)
+    S* PE = (S*)I.PE;
+    S* PR = (S*)I.PR;
+    const int CH = I.CH, Rp = I.Rp, kp = I.kp;
+    const size_t total = (size_t)I.ntile * Rp * CH;
+    for (size_t e = tid; e < total; e += nth) {
+        const int ii = (int)(e % CH);
+        const int r = (int)((e / CH) % Rp);
+        const int t = (int)(e / ((size_t)CH * Rp));
+        const int i = t * CH + ii;
+        double v = 0.0;
+        if (i < n) {
+            if (r < k) v = (double)F[(size_t)i * k + r];
+            else if (r >= kp && r < kp + m) v = (double)A[(size_t)(r - kp) * n + i];
+        }
+        const S sv = to_s<S>(v);
+        PE[e] = sv;
+        PR[((size_t)t * CH + ii) * Rp + r] = sv;
     }
     const int nOm = I.omega_diag ? k : k * k;
     for (size_t e = tid; e < (size_t)nOm; e += nth) ((double*)I.Om)[e] = (double)Om[e];
@@ -237,8 +260,10 @@ Inst<M, S> carve(const ff_problem& p, const Sizes& s, unsigned char*& cur, void*
     I.omega_diag = p.omega_diag ? 1 : 0;
     auto take = [&](size_t bytes) { unsigned char* r = cur; cur += a256(bytes); return (void*)r; };
     const size_t r = sizeof(double);
-    I.Ft = (const S*)take(2 * (size_t)s.k * s.np * sizeof(S));
-    I.At = (const S*)take(2 * (size_t)s.m * s.np * sizeof(S) + 16);
+    I.CH = s.tl.CH; I.kp = s.tl.kp; I.mp = s.tl.mp; I.Rp = s.tl.Rp; I.ntile = s.tl.ntile;
+    const size_t pb = (size_t)s.tl.ntile * s.tl.Rp * s.tl.CH * sizeof(S);
+    I.PE = (const S*)take(pb);
+    I.PR = (const S*)take(pb);
     I.Om = (const double*)take((size_t)(I.omega_diag ? s.k : s.k * s.k) * r);
     I.alpha = (const double*)take((size_t)s.P * s.np * r);
     I.Dp = (const double*)take((size_t)s.P * s.np * r);
@@ -354,6 +379,7 @@ Params make_params(const ff_options& o) {
     prm.rho = o.reflection;
     prm.beta_suff = o.restart_sufficient;
     prm.beta_nec = o.restart_necessary;
+    prm.beta_art = o.restart_artificial;
     prm.step_fraction = o.step_fraction;
     prm.beta = o.beta;
     prm.power_iters = 60;
@@ -374,7 +400,7 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
     std::vector<Sizes> sz(count);
     size_t need = table_bytes<M, S>(count);
     for (int t = 0; t < count; ++t) {
-        sz[t] = sizes_of(probs[t]);
+        sz[t] = sizes_of(probs[t], o.precision);
         if (!supported(sz[t], probs[t].omega_diag, o.precision)) return FF_ERR_UNSUPPORTED;
         need += inst_bytes(sz[t], probs[t].omega_diag, o.precision);
     }
@@ -407,7 +433,8 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
         table[slot] = carve<M, S>(probs[t], sz[t], cur, w_out[t], yA_out ? yA_out[t] : nullptr,
                                   yD_out ? yD_out[t] : nullptr, res + t);
         pslot[slot] = probs[t];
-        maxel = std::max(maxel, (long long)sz[t].np * std::max(std::max(sz[t].k, sz[t].m), sz[t].P + sz[t].R));
+        maxel = std::max(maxel, std::max((long long)sz[t].tl.ntile * sz[t].tl.Rp * sz[t].tl.CH,
+                                         (long long)sz[t].np * (sz[t].P + sz[t].R)));
     }
     // groups: [first slot, end slot) of equal G and kind (single- or
     // multi-period), at most kMaxGroups
@@ -434,8 +461,7 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
         size_t smem = 0;
         for (int slot = gfirst[gi]; slot < gfirst[gi + 1]; ++slot) {
             const int t = order[slot];
-            smem = std::max(smem, solver_smem_bytes(sz[t].P, sz[t].k, sz[t].m, probs[t].omega_diag,
-                                                    matvec_elem(o.precision)));
+            smem = std::max(smem, smem_of(sz[t], o.precision));
         }
         int maxc = 0;
         for (;;) {
@@ -551,7 +577,7 @@ void* static_workspace() {
 template <class M, class S>
 int run_single_static(const ff_problem& p, const ff_options& o, ff_result* res, void* w_out, void* yA_out,
                       void* yD_out, cudaStream_t stream) {
-    const Sizes sz = sizes_of(p);
+    const Sizes sz = sizes_of(p, o.precision);
     if (!supported(sz, p.omega_diag, o.precision)) return FF_ERR_UNSUPPORTED;
     constexpr size_t kInstBytes = c_a256(sizeof(Inst<M, S>));
     constexpr size_t kStage = kInstBytes + c_a256(sizeof(ff_problem));
@@ -576,12 +602,12 @@ int run_single_static(const ff_problem& p, const ff_options& o, ff_result* res, 
     if (e != cudaSuccess) return cuda_fail(e, "copy of the instance record");
     const Inst<M, S>* table_dev = (const Inst<M, S>*)base;
     const ff_problem* prob_dev = (const ff_problem*)(base + kInstBytes);
-    long long maxel = (long long)sz.np * std::max(std::max(sz.k, sz.m), sz.P + sz.R);
+    long long maxel = std::max((long long)sz.tl.ntile * sz.tl.Rp * sz.tl.CH, (long long)sz.np * (sz.P + sz.R));
     const int bx = (int)std::min<long long>(64, (maxel + 255) / 256);
     repack_batch_kernel<M, S><<<dim3((unsigned)std::max(bx, 1), 1u), 256, 0, stream>>>(prob_dev, table_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "repack launch");
-    const size_t smem = solver_smem_bytes(sz.P, sz.k, sz.m, p.omega_diag, matvec_elem(o.precision));
+    const size_t smem = smem_of(sz, o.precision);
     const int G = o.cluster_size > 0 ? o.cluster_size : auto_cluster(sz, 1);
     int maxc = 0;
     e = max_teams<M, S>(G, smem, true, &maxc);
@@ -628,7 +654,7 @@ size_t ff_workspace_size(const ff_problem* probs, int count, const ff_options* o
     size_t need = ff::table_bytes_of(o.precision, count);
     for (int t = 0; t < count; ++t) {
         if (!ff::valid_problem(&probs[t])) return 0;
-        need += ff::inst_bytes(ff::sizes_of(probs[t]), probs[t].omega_diag, o.precision);
+        need += ff::inst_bytes(ff::sizes_of(probs[t], o.precision), probs[t].omega_diag, o.precision);
     }
     return need;
 }
@@ -665,7 +691,7 @@ int ff_batch_plan(const ff_problem* probs, int count, const ff_options* o_in, in
     std::vector<ff::Sizes> sz(count);
     for (int t = 0; t < count; ++t) {
         if (!ff::valid_problem(&probs[t])) return FF_ERR_INVALID_ARG;
-        sz[t] = ff::sizes_of(probs[t]);
+        sz[t] = ff::sizes_of(probs[t], o.precision);
     }
     std::vector<int> G;
     if (o.cluster_size > 0) G.assign(count, o.cluster_size);

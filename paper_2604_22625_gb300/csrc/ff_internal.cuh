@@ -15,17 +15,43 @@ constexpr int kPC = 8;                 // periods processed together in a matvec
 constexpr int kCand = 8;               // threshold candidates per period and search round
 constexpr int kMaxRounds = 16;         // threshold search rounds per projection
 constexpr int kMaxCluster = 16;
-constexpr int kSingleCtasPerSm = 1;    // resident CTAs per SM the single-period variant is built for
+constexpr int kSingleCtasPerSm = 1;
+constexpr int kStallChecks = 48;       // checks without halving the KKT before FP64 escalation    // resident CTAs per SM the single-period variant is built for
+
+constexpr int kStages = 3;             // bulk-copy ring stages per CTA
+constexpr int kMaxTileBytes = 48 * 1024;
+constexpr int kSmemLimit = 227 * 1024 - 2048;   // dynamic shared memory per CTA we allow ourselves
+
+// Panel tiling: the rows of F^T (k, padded to kp) and of A (m, padded to mp)
+// form one panel of Rp = kp + mp rows; the assets are cut into tiles of CH.
+// Two tiled copies exist: PE (tile = Rp rows x CH assets, assets contiguous)
+// feeds the expand pass, PR (tile = CH assets x Rp rows, rows contiguous)
+// feeds the reduce pass.  A tile is one contiguous block of Rp * CH elements
+// that one bulk copy moves into shared memory.
+struct Tiling {
+    int CH, kp, mp, Rp, ntile;
+};
+
+__host__ __device__ inline Tiling make_tiling(int n, int k, int m, int CH) {
+    Tiling t;
+    t.CH = CH;
+    t.kp = (k + 7) / 8 * 8;
+    t.mp = (m + 7) / 8 * 8;
+    t.Rp = t.kp + t.mp;
+    t.ntile = (n + CH - 1) / CH;
+    return t;
+}
 
 // One instance as the solver kernel sees it (device memory).  All per-asset
-// arrays have row stride np (n rounded up to a multiple of 32).  Panels are
-// stored as S (double, float or bfloat16) and multiplied in M (double or
+// state arrays have row stride np (n rounded up to a multiple of 32).  Panels
+// are stored as S (double, float or bfloat16) and multiplied in M (double or
 // float); the iterate state and every elementwise update are FP64.
 template <class M, class S>
 struct Inst {
     int n, k, m, P, R, multi, np, omega_diag;
-    const S* Ft;          // k x np factor-major F^T, followed by np x k asset-major F
-    const S* At;          // m x np exposure rows, followed by np x m asset-major A^T
+    int CH, kp, mp, Rp, ntile; // panel tiling (see Tiling)
+    const S* PE;          // ntile tiles of [Rp][CH]
+    const S* PR;          // ntile tiles of [CH][Rp]
     const double* Om;     // k x k, or k diagonal entries
     const double* alpha;  // P x np
     const double* Dp;     // P x np
@@ -58,7 +84,7 @@ struct Params {
     double time_limit_ns;
     int check_every;
     double rho;
-    double beta_suff, beta_nec;
+    double beta_suff, beta_nec, beta_art;
     double step_fraction;
     double beta;
     int power_iters;
@@ -66,8 +92,12 @@ struct Params {
                          // instances from it in table order
 };
 
-// Shared-memory bytes the solver kernel needs for these sizes.
-size_t solver_smem_bytes(int P, int k, int m, int omega_diag, size_t matvec_size);
+// Shared-memory bytes the solver kernel needs for these sizes and tiling.
+size_t solver_smem_bytes(int P, int k, int m, int omega_diag, size_t matvec_size, int CH, int Rp, size_t panel_size);
+
+// Largest tile width CH (256 down to 8) whose shared-memory layout fits;
+// 0 if none does.
+int choose_tile(int P, int k, int m, int omega_diag, size_t matvec_size, size_t panel_size);
 
 // Launch the team kernel over `count` instances (insts is a device array).
 // G = CTAs per instance (cluster size), nteams = concurrent teams; single =

@@ -31,6 +31,8 @@
 #include <cooperative_groups.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "ff_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -41,10 +43,11 @@ namespace ff {
 // shared-memory layout (identical on host and device)
 // ---------------------------------------------------------------------------
 struct Layout {
-    size_t vpart, vout;        // double, vlen each (one chunk of kPC periods)
+    size_t vpart, vout;        // double, vlen each (one chunk of periods; vpart also holds the
+                               // expand pass's cross-split partial sums)
     size_t spart, sout;        // double, slen each
     size_t wred;               // double, kWarps * 32
-    size_t stage;              // M, 2048 (4 vectors x PCT periods x 512/PCT assets)
+    size_t stage;              // M, 4 vectors x PCT periods x CH assets (reduce pass)
     size_t yA, yAb, ax;        // double, P*m each
     size_t u, ub;              // double, P*k each
     size_t om;                 // M, P*k
@@ -52,27 +55,37 @@ struct Layout {
     size_t Om;                 // double, k*k or k
     size_t cand, thprev, theta, thq;
     size_t lb, ubd;            // double, m each
+    size_t bars;               // kStages mbarriers
+    size_t ring;               // kStages panel tiles
+    size_t tile_bytes;
     size_t total;
     int vlen, slen;
 };
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-__host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_diag, size_t ms) {
+__host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_diag, size_t ms, int CH, int Rp,
+                                              size_t ps) {
     Layout L;
-    L.vlen = (P < kPC ? P : kPC) * (2 * m + 2 * k);
+    const int pct0 = P < kPC ? P : kPC;
+    const int pct = pct0 <= 1 ? 1 : (pct0 <= 2 ? 2 : (pct0 <= 4 ? 4 : 8));   // template chunk width
+    L.vlen = pct0 * (2 * m + 2 * k);
     const int slots = (kWarps * P * kCand + 1) / 2;   // 4-byte threshold slots in 8-byte units
     if (L.vlen < slots) L.vlen = slots;
+    // the expand pass's cross-split partials (kThreads x 2 x pct, up to double)
+    // occupy vpart and vout together
+    if (L.vlen < kThreads * pct) L.vlen = kThreads * pct;
     int s1 = P * kCand * 2, s2 = P + 48;
     L.slen = s1 > s2 ? s1 : s2;
     size_t o = 0;
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes + 16, 16); return r; };
+    L.bars = take((size_t)kStages * 8);   // first: the barriers keep their place across instances
     L.vpart = take((size_t)L.vlen * 8);
     L.vout = take((size_t)L.vlen * 8);
     L.spart = take((size_t)L.slen * 8);
     L.sout = take((size_t)L.slen * 8);
     L.wred = take((size_t)kWarps * 32 * 8);
-    L.stage = take((size_t)2048 * ms);              // 4 vectors x PCT periods x 512/PCT assets
+    L.stage = take((size_t)4 * pct * CH * (ms > 8 ? ms : 8));   // staged as M, or double at checks
     L.yA = take((size_t)P * m * 8);
     // whole chunks for the expand pass weights (a single period needs no padding)
     const int Pr = P <= 1 ? 1 : (P + kPC - 1) / kPC * kPC;
@@ -89,12 +102,108 @@ __host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_dia
     L.thq = take((size_t)P * 8);
     L.lb = take((size_t)m * 8);
     L.ubd = take((size_t)m * 8);
+    o = align_up(o, 128);
+    L.tile_bytes = align_up((size_t)Rp * CH * ps, 128);
+    L.ring = o;
+    o += (size_t)kStages * L.tile_bytes;
     L.total = o;
     return L;
 }
 
-size_t solver_smem_bytes(int P, int k, int m, int omega_diag, size_t matvec_size) {
-    return make_layout(P, k, m, omega_diag, matvec_size).total;
+size_t solver_smem_bytes(int P, int k, int m, int omega_diag, size_t matvec_size, int CH, int Rp,
+                         size_t panel_size) {
+    return make_layout(P, k, m, omega_diag, matvec_size, CH, Rp, panel_size).total;
+}
+
+int choose_tile(int P, int k, int m, int omega_diag, size_t matvec_size, size_t panel_size) {
+    const int Rp = (k + 7) / 8 * 8 + (m + 7) / 8 * 8;
+    for (int CH = 256; CH >= 8; CH /= 2) {
+        if ((size_t)Rp * CH * panel_size > (size_t)kMaxTileBytes) continue;
+        if (make_layout(P, k, m, omega_diag, matvec_size, CH, Rp, panel_size).total <= (size_t)kSmemLimit)
+            return CH;
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// bulk-copy ring: one thread issues cp.async.bulk copies of whole panel tiles
+// into kStages shared-memory stages, each completing on its own mbarrier.
+// Every thread keeps an identical copy of the ring state (all follow the same
+// sequence of waits), so stage indices and phase parities need no sharing.
+// ---------------------------------------------------------------------------
+struct Pipe {
+    unsigned char* ring;
+    unsigned long long* bars;
+    size_t stride;            // bytes per stage (the instance's tile bytes, 128-aligned)
+    int head;                 // next stage to consume
+    int tail;                 // next stage to fill
+    int inflight;             // copies issued and not yet consumed
+    unsigned phase;           // bit s: parity of the phase stage s completes next
+    int* err;                 // shared flag: a bounded wait expired
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+// thread 0 of the CTA initialises the barriers (once per kernel)
+__device__ __forceinline__ void pipe_init(Pipe& pp) {
+    if (threadIdx.x == 0) {
+        for (int s2 = 0; s2 < kStages; ++s2)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&pp.bars[s2])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+}
+
+// Issue the copy of `bytes` from global `src` into the tail stage.  Called by
+// every thread (uniform), performed by thread 0.
+__device__ __forceinline__ void pipe_issue(Pipe& pp, const void* src, unsigned bytes) {
+    if (threadIdx.x == 0) {
+        const unsigned bar = smem_u32(&pp.bars[pp.tail]);
+        const unsigned dst = smem_u32(pp.ring + (size_t)pp.tail * pp.stride);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+                     : "memory");
+    }
+    pp.tail = pp.tail + 1 == kStages ? 0 : pp.tail + 1;
+    ++pp.inflight;
+}
+
+// Wait (bounded) until the head stage has landed; returns its shared address.
+// On expiry the shared error flag is set and the stage is used as it is (the
+// instance then ends with FF_STALLED at its next check).
+__device__ __forceinline__ const unsigned char* pipe_wait(Pipe& pp) {
+    const unsigned bar = smem_u32(&pp.bars[pp.head]);
+    const unsigned parity = (pp.phase >> pp.head) & 1u;
+    unsigned done = 0;
+    for (int spin = 0; spin < (1 << 22); ++spin) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) break;
+    }
+    if (!done) *pp.err = 1;
+    return pp.ring + (size_t)pp.head * pp.stride;
+}
+
+// The head stage has been read by every thread (caller synchronised): move on.
+__device__ __forceinline__ void pipe_pop(Pipe& pp) {
+    pp.phase ^= 1u << pp.head;
+    pp.head = pp.head + 1 == kStages ? 0 : pp.head + 1;
+    --pp.inflight;
+}
+
+// Before the CTA leaves an instance on an error, let copies still in flight land.
+__device__ void pipe_drain(Pipe& pp) {
+    while (pp.inflight > 0) {
+        pipe_wait(pp);
+        __syncthreads();
+        pipe_pop(pp);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -196,7 +305,9 @@ struct Ctx {
     Inst<M, S> I;
     int n, k, m, P, R, np;
     int i0, i1;
+    int t0, t1;                // panel tiles of this CTA
     int G, g;
+    Pipe pipe;
     int tid, lane, warp;
     double *vpart, *vout, *spart, *sout, *wred;
     M* stage;
@@ -272,8 +383,27 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
-// chunk geometry of the reduce pass: PCT periods x CH assets staged per step
-template <int PCT> struct Chunk { static constexpr int CH = 512 / PCT; };
+// RPT consecutive panel rows of one asset from a PR tile (shared memory)
+template <class M, class S> struct RowLoad;
+template <class M> struct RowLoad<M, __nv_bfloat16> {
+    static __device__ __forceinline__ void load(const __nv_bfloat16* p, M (&w)[4]) {
+        const uint2 u = *(const uint2*)p;
+        const __nv_bfloat162 a = *(const __nv_bfloat162*)&u.x, b = *(const __nv_bfloat162*)&u.y;
+        w[0] = (M)__low2float(a); w[1] = (M)__high2float(a); w[2] = (M)__low2float(b); w[3] = (M)__high2float(b);
+    }
+};
+template <class M> struct RowLoad<M, float> {
+    static __device__ __forceinline__ void load(const float* p, M (&w)[4]) {
+        const float4 u = *(const float4*)p;
+        w[0] = (M)u.x; w[1] = (M)u.y; w[2] = (M)u.z; w[3] = (M)u.w;
+    }
+};
+template <class M> struct RowLoad<M, double> {
+    static __device__ __forceinline__ void load(const double* p, M (&w)[4]) {
+        const double2 a = *(const double2*)p, b = *(const double2*)(p + 2);
+        w[0] = (M)a.x; w[1] = (M)a.y; w[2] = (M)b.x; w[3] = (M)b.y;
+    }
+};
 
 // ---------------------------------------------------------------------------
 // reduce pass over one chunk of periods [p0, p0 + pc), pc <= PCT:
@@ -281,31 +411,40 @@ template <int PCT> struct Chunk { static constexpr int CH = 512 / PCT; };
 //   vpart[q*Lr + m + j]      = sum_i A_ji a1_{p0+q, i}
 //   vpart[q*Lr + 2m + j]     = sum_i F_ij (f0_{p0+q, i} - c_i)   (j < k)
 //   vpart[q*Lr + 2m + k + j] = sum_i F_ij (f1_{p0+q, i} - c_i)
-// with Lr = 2m + 2k, over the CTA's assets.  Thread per output row (asset-major
-// panels: consecutive rows are contiguous, so a warp's loads coalesce), vectors
-// staged through shared memory CH assets at a time, products and chunk sums in
-// M, chunk sums added in FP64.  Null vectors give zeros.
+// with Lr = 2m + 2k, over the CTA's assets.  The PR tiles stream through the
+// bulk-copy ring; the vectors of a tile are staged in shared memory as M while
+// its copy is in flight.  Thread mapping: groups of na consecutive threads own
+// 4 consecutive panel rows, the na lanes of a group take every na-th asset of
+// the tile.  Products and per-tile sums in M (at most CH / na terms), lanes
+// combined by warp shuffles, tile sums added into vpart in FP64 by the group's
+// first lane (one owner per entry: no races, fixed order).  Null vectors give
+// zeros.
 // ---------------------------------------------------------------------------
-template <int PCT, class M, class S>
+template <int PCT, class AT, class M, class S>
 __device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, const double* a1,
                                const double* f0, const double* f1, bool subcen) {
-    constexpr int CH = Chunk<PCT>::CH;
-    const int m = c.m, k = c.k, np = c.np;
-    const int rows = m + k;
+    constexpr int RPT = 4;
+    const int CH = c.I.CH, Rp = c.I.Rp, kp = c.I.kp;
+    const int m = c.m, k = c.k, np = c.np, n = c.n;
     const int Lr = 2 * m + 2 * k;
-    const S* Fam = c.I.Ft + (size_t)k * np;
-    const S* Aam = c.I.At + (size_t)m * np;
-    M* st = c.stage;  // [4][PCT][CH]
-    double acc[2][2][PCT];
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-        for (int t = 0; t < 2; ++t)
-#pragma unroll
-            for (int q = 0; q < PCT; ++q) acc[s][t][q] = 0;
+    const int ngr = Rp / RPT;
+    int na = 1;
+    while (na < 32 && ngr * na * 2 <= kThreads) na *= 2;
+    const int grp = c.tid / na, lane_a = c.tid % na;
+    const bool active = grp < ngr;
+    const int r0 = grp * RPT;
+    const bool isA = r0 >= kp;
     const bool has1 = (a1 != nullptr) || (f1 != nullptr);
-    for (int ib = c.i0; ib < c.i1; ib += CH) {
-        const int cnt = min(CH, c.i1 - ib);
+    const size_t tile_elems = (size_t)Rp * CH;
+    const unsigned bytes = (unsigned)(tile_elems * sizeof(S));
+    AT* st = (AT*)c.stage;  // [4][PCT][CH]
+    for (int e = c.tid; e < pc * Lr; e += kThreads) c.vpart[e] = 0;
+    const int nt = c.t1 - c.t0;
+    for (int j = 0; j < nt && j < kStages; ++j) pipe_issue(c.pipe, c.I.PR + (size_t)(c.t0 + j) * tile_elems, bytes);
+    for (int j = 0; j < nt; ++j) {
+        const int t = c.t0 + j;
+        const int ib = t * CH;
+        const int cnt = min(CH, n - ib);
         for (int e = c.tid; e < 4 * PCT * CH; e += kThreads) {
             const int vec = e / (PCT * CH);
             const int q = (e / CH) % PCT;
@@ -316,155 +455,195 @@ __device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, c
                 const int i = ib + ii;
                 val = src[(size_t)(p0 + q) * np + i] - ((subcen && vec >= 2) ? c.I.cen[i] : 0.0);
             }
-            st[e] = (M)val;
+            st[e] = (AT)val;
         }
+        const S* tile = (const S*)pipe_wait(c.pipe);
         __syncthreads();
+        AT acc[RPT][2][PCT];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const int row = c.tid + s * kThreads;
-            if (row < rows) {
-                const bool isA = row < m;
-                const int j = isA ? row : row - m;
-                const S* base = isA ? (Aam + (size_t)ib * m + j) : (Fam + (size_t)ib * k + j);
-                const int stride = isA ? m : k;
-                const M* sv0 = st + (isA ? 0 : 2) * PCT * CH;
-                const M* sv1 = st + (isA ? 1 : 3) * PCT * CH;
-                M a[2][PCT];
+        for (int r = 0; r < RPT; ++r)
 #pragma unroll
-                for (int q = 0; q < PCT; ++q) { a[0][q] = 0; a[1][q] = 0; }
-                int ii = 0;
-                for (; ii + 8 <= cnt; ii += 8) {
-                    M w[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) w[u] = ldp<M, S>(base + (size_t)(ii + u) * stride);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-#pragma unroll
-                        for (int q = 0; q < PCT; ++q) {
-                            a[0][q] += w[u] * sv0[q * CH + ii + u];
-                            if (has1) a[1][q] += w[u] * sv1[q * CH + ii + u];
-                        }
-                }
-                for (; ii < cnt; ++ii) {
-                    const M w = ldp<M, S>(base + (size_t)ii * stride);
-#pragma unroll
-                    for (int q = 0; q < PCT; ++q) {
-                        a[0][q] += w * sv0[q * CH + ii];
-                        if (has1) a[1][q] += w * sv1[q * CH + ii];
-                    }
-                }
+            for (int q = 0; q < PCT; ++q) { acc[r][0][q] = 0; acc[r][1][q] = 0; }
+        if (active) {
+            const AT* sv0 = st + (isA ? 0 : 2) * PCT * CH;
+            const AT* sv1 = st + (isA ? 1 : 3) * PCT * CH;
+            for (int ii = lane_a; ii < cnt; ii += na) {
+                AT w[RPT];
+                RowLoad<AT, S>::load(tile + (size_t)ii * Rp + r0, w);
 #pragma unroll
                 for (int q = 0; q < PCT; ++q) {
-                    acc[s][0][q] += (double)a[0][q];
-                    acc[s][1][q] += (double)a[1][q];
-                }
-            }
-        }
-        __syncthreads();
-    }
+                    const AT x0 = sv0[q * CH + ii];
+                    const AT x1 = has1 ? sv1[q * CH + ii] : (AT)0;
 #pragma unroll
-    for (int s = 0; s < 2; ++s) {
-        const int row = c.tid + s * kThreads;
-        if (row < rows) {
-            const bool isA = row < m;
-            const int j = isA ? row : row - m;
-#pragma unroll
-            for (int q = 0; q < PCT; ++q) {
-                if (q < pc) {
-                    if (isA) {
-                        c.vpart[q * Lr + j] = acc[s][0][q];
-                        c.vpart[q * Lr + m + j] = acc[s][1][q];
-                    } else {
-                        c.vpart[q * Lr + 2 * m + j] = acc[s][0][q];
-                        c.vpart[q * Lr + 2 * m + k + j] = acc[s][1][q];
+                    for (int r = 0; r < RPT; ++r) {
+                        acc[r][0][q] += w[r] * x0;
+                        acc[r][1][q] += w[r] * x1;
                     }
                 }
             }
         }
+        for (int off = na / 2; off > 0; off >>= 1) {
+#pragma unroll
+            for (int r = 0; r < RPT; ++r)
+#pragma unroll
+                for (int q = 0; q < PCT; ++q) {
+                    acc[r][0][q] += __shfl_xor_sync(0xffffffffu, acc[r][0][q], off);
+                    acc[r][1][q] += __shfl_xor_sync(0xffffffffu, acc[r][1][q], off);
+                }
+        }
+        if (active && lane_a == 0) {
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                const int row = r0 + r;
+                int o0 = -1, o1 = -1;
+                if (!isA && row < k) { o0 = 2 * m + row; o1 = 2 * m + k + row; }
+                if (isA && row - kp < m) { o0 = row - kp; o1 = m + row - kp; }
+                if (o0 >= 0) {
+#pragma unroll
+                    for (int q = 0; q < PCT; ++q) {
+                        if (q < pc) {
+                            c.vpart[q * Lr + o0] += (double)acc[r][0][q];
+                            c.vpart[q * Lr + o1] += (double)acc[r][1][q];
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        pipe_pop(c.pipe);
+        if (j + kStages < nt) pipe_issue(c.pipe, c.I.PR + (size_t)(t + kStages) * tile_elems, bytes);
     }
     __syncthreads();
 }
 
 // PCMAX = 1: the kernel variant for single-period instances (only the
 // one-period code is instantiated, which keeps its register count low)
-template <int PCMAX, class M, class S>
+// AT: arithmetic of the products and tile sums (M, or double for the FP64
+// pass of the KKT check)
+template <int PCMAX, class AT = void, class M, class S>
 __device__ void reduce_chunk(Ctx<M, S>& c, int p0, int pc, const double* a0, const double* a1, const double* f0,
                              const double* f1, bool subcen) {
+    using T = typename std::conditional<std::is_same<AT, void>::value, M, AT>::type;
     if constexpr (PCMAX == 1) {
-        reduce_chunk_t<1>(c, p0, pc, a0, a1, f0, f1, subcen);
+        reduce_chunk_t<1, T>(c, p0, pc, a0, a1, f0, f1, subcen);
     } else {
-        if (pc <= 1) reduce_chunk_t<1>(c, p0, pc, a0, a1, f0, f1, subcen);
-        else if (pc <= 2) reduce_chunk_t<2>(c, p0, pc, a0, a1, f0, f1, subcen);
-        else if (pc <= 4) reduce_chunk_t<4>(c, p0, pc, a0, a1, f0, f1, subcen);
-        else reduce_chunk_t<8>(c, p0, pc, a0, a1, f0, f1, subcen);
+        if (pc <= 1) reduce_chunk_t<1, T>(c, p0, pc, a0, a1, f0, f1, subcen);
+        else if (pc <= 2) reduce_chunk_t<2, T>(c, p0, pc, a0, a1, f0, f1, subcen);
+        else if (pc <= 4) reduce_chunk_t<4, T>(c, p0, pc, a0, a1, f0, f1, subcen);
+        else reduce_chunk_t<8, T>(c, p0, pc, a0, a1, f0, f1, subcen);
     }
 }
 
 // ---------------------------------------------------------------------------
 // expand pass: for every local asset i and period p < Pv,
 //   epi(i, p, (F wF_p)_i, (A^T wA_p)_i)     with wF (Pv x k), wA (Pv x m)
-// arithmetic in A (M or double), factor-major panels (a warp's loads coalesce
-// along the assets).
+// arithmetic in A (M or double).  The PE tiles ([Rp][CH], assets contiguous)
+// stream through the bulk-copy ring.  Thread mapping inside a tile: asset
+// ii = tid % CH, row split rs = tid / CH (RS = kThreads / CH splits, each a
+// contiguous share of the F rows and of the A rows); the splits' partial sums
+// meet in shared memory (vpart..vout) and the (asset, period) epilogues are
+// spread over all threads.
 // ---------------------------------------------------------------------------
 template <int PCT, class A, class M, class S, class W, class Epi>
-__device__ void expand_chunk(Ctx<M, S>& c, int i, int p0, int pc, const W* wF, const W* wA, Epi& epi) {
-    const int m = c.m, k = c.k, np = c.np;
+__device__ void expand_tile(Ctx<M, S>& c, const S* tile, int ib, int cnt, int p0, int pc, const W* wF,
+                            const W* wA, Epi& epi) {
+    const int CH = c.I.CH, kp = c.I.kp, k = c.k, m = c.m;
+    const int RS = kThreads / CH;
+    const int ii = c.tid % CH, rs = c.tid / CH;
     A aF[PCT], aA[PCT];
 #pragma unroll
     for (int q = 0; q < PCT; ++q) { aF[q] = 0; aA[q] = 0; }
     const W* wf = wF + (size_t)p0 * k;
     const W* wa = wA + (size_t)p0 * m;
-    int j = 0;
-    for (; j + 4 <= k; j += 4) {
+    const int jf0 = k * rs / RS, jf1 = k * (rs + 1) / RS;
+    const int ja0 = m * rs / RS, ja1 = m * (rs + 1) / RS;
+    int j = jf0;
+    for (; j + 4 <= jf1; j += 4) {
         A f[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) f[u] = ldp<A, S>(c.I.Ft + (size_t)(j + u) * np + i);
+        for (int u = 0; u < 4; ++u) f[u] = (A)cvt(tile[(size_t)(j + u) * CH + ii]);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int q = 0; q < PCT; ++q) aF[q] += f[u] * (A)wf[q * k + j + u];
     }
-    for (; j < k; ++j) {
-        const A f = ldp<A, S>(c.I.Ft + (size_t)j * np + i);
+    for (; j < jf1; ++j) {
+        const A f = (A)cvt(tile[(size_t)j * CH + ii]);
 #pragma unroll
         for (int q = 0; q < PCT; ++q) aF[q] += f * (A)wf[q * k + j];
     }
-    j = 0;
-    for (; j + 4 <= m; j += 4) {
+    j = ja0;
+    for (; j + 4 <= ja1; j += 4) {
         A a[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = ldp<A, S>(c.I.At + (size_t)(j + u) * np + i);
+        for (int u = 0; u < 4; ++u) a[u] = (A)cvt(tile[(size_t)(kp + j + u) * CH + ii]);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int q = 0; q < PCT; ++q) aA[q] += a[u] * (A)wa[q * m + j + u];
     }
-    for (; j < m; ++j) {
-        const A a = ldp<A, S>(c.I.At + (size_t)j * np + i);
+    for (; j < ja1; ++j) {
+        const A a = (A)cvt(tile[(size_t)(kp + j) * CH + ii]);
 #pragma unroll
         for (int q = 0; q < PCT; ++q) aA[q] += a * (A)wa[q * m + j];
     }
+    if (RS == 1) {
+        if (ii < cnt) {
 #pragma unroll
-    for (int q = 0; q < PCT; ++q)
-        if (q < pc) epi(i, p0 + q, (double)aF[q], (double)aA[q]);
+            for (int q = 0; q < PCT; ++q)
+                if (q < pc) epi(ib + ii, p0 + q, (double)aF[q], (double)aA[q]);
+        }
+        return;
+    }
+    A* red = (A*)c.vpart;   // [RS][CH][2][PCT]
+#pragma unroll
+    for (int q = 0; q < PCT; ++q) {
+        red[(((size_t)rs * CH + ii) * 2 + 0) * PCT + q] = aF[q];
+        red[(((size_t)rs * CH + ii) * 2 + 1) * PCT + q] = aA[q];
+    }
+    __syncthreads();
+    for (int e = c.tid; e < CH * pc; e += kThreads) {
+        const int i2 = e % CH, q = e / CH;
+        if (i2 < cnt) {
+            A sF = 0, sA = 0;
+            for (int r = 0; r < RS; ++r) {
+                sF += red[(((size_t)r * CH + i2) * 2 + 0) * PCT + q];
+                sA += red[(((size_t)r * CH + i2) * 2 + 1) * PCT + q];
+            }
+            epi(ib + i2, p0 + q, (double)sF, (double)sA);
+        }
+    }
+    __syncthreads();
 }
 
 // The weight vectors must have PCT rows readable past Pv: callers size the
 // replicated arrays for whole chunks (rows beyond Pv hold finite values).
 template <class A, int PCMAX, class M, class S, class W, class Epi>
 __device__ void expand_pass(Ctx<M, S>& c, int Pv, const W* wF, const W* wA, Epi epi) {
-    for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
+    const int CH = c.I.CH;
+    const size_t tile_elems = (size_t)c.I.Rp * CH;
+    const unsigned bytes = (unsigned)(tile_elems * sizeof(S));
+    const int nt = c.t1 - c.t0;
+    for (int j = 0; j < nt && j < kStages; ++j) pipe_issue(c.pipe, c.I.PE + (size_t)(c.t0 + j) * tile_elems, bytes);
+    for (int j = 0; j < nt; ++j) {
+        const int t = c.t0 + j;
+        const int ib = t * CH;
+        const int cnt = min(CH, c.n - ib);
+        const S* tile = (const S*)pipe_wait(c.pipe);
         if constexpr (PCMAX == 1) {
-            expand_chunk<1, A>(c, i, 0, 1, wF, wA, epi);
+            expand_tile<1, A>(c, tile, ib, cnt, 0, 1, wF, wA, epi);
         } else {
             for (int p0 = 0; p0 < Pv; p0 += kPC) {
                 const int pc = min(kPC, Pv - p0);
-                if (pc <= 1) expand_chunk<1, A>(c, i, p0, pc, wF, wA, epi);
-                else if (pc <= 2) expand_chunk<2, A>(c, i, p0, pc, wF, wA, epi);
-                else if (pc <= 4) expand_chunk<4, A>(c, i, p0, pc, wF, wA, epi);
-                else expand_chunk<8, A>(c, i, p0, pc, wF, wA, epi);
+                if (pc <= 1) expand_tile<1, A>(c, tile, ib, cnt, p0, pc, wF, wA, epi);
+                else if (pc <= 2) expand_tile<2, A>(c, tile, ib, cnt, p0, pc, wF, wA, epi);
+                else if (pc <= 4) expand_tile<4, A>(c, tile, ib, cnt, p0, pc, wF, wA, epi);
+                else expand_tile<8, A>(c, tile, ib, cnt, p0, pc, wF, wA, epi);
             }
         }
+        __syncthreads();
+        pipe_pop(c.pipe);
+        if (j + kStages < nt) pipe_issue(c.pipe, c.I.PE + (size_t)(t + kStages) * tile_elems, bytes);
     }
 }
 
@@ -616,6 +795,18 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
     const int G = (int)cl.num_blocks();
     const int g = (int)cl.block_rank();
     __shared__ int next_s;
+    __shared__ int pipe_err_s;
+    Pipe pipe;
+    pipe.bars = (unsigned long long*)smem;   // the layout puts the barriers first
+    pipe.ring = nullptr;
+    pipe.stride = 0;
+    pipe.head = 0;
+    pipe.tail = 0;
+    pipe.inflight = 0;
+    pipe.phase = 0;
+    pipe.err = &pipe_err_s;
+    if (threadIdx.x == 0) pipe_err_s = 0;
+    pipe_init(pipe);
 
     for (;;) {
         // the team's rank-0 thread takes the next instance from the queue and
@@ -632,11 +823,17 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         c.R = PCMAX == 1 ? 1 : c.I.R;
         c.G = G; c.g = g;
         c.tid = threadIdx.x; c.lane = threadIdx.x & 31; c.warp = threadIdx.x >> 5;
-        c.i0 = (int)(((long long)c.n * g) / G);
-        c.i1 = (int)(((long long)c.n * (g + 1)) / G);
+        c.t0 = (int)(((long long)c.I.ntile * g) / G);
+        c.t1 = (int)(((long long)c.I.ntile * (g + 1)) / G);
+        c.i0 = min(c.n, c.t0 * c.I.CH);
+        c.i1 = min(c.n, c.t1 * c.I.CH);
         const int n = c.n, k = c.k, m = c.m, P = c.P, R = c.R, np = c.np;
         const int Lr = 2 * m + 2 * k;
-        const Layout Ly = make_layout(P, k, m, c.I.omega_diag, sizeof(M));
+        const Layout Ly = make_layout(P, k, m, c.I.omega_diag, sizeof(M), c.I.CH, c.I.Rp, sizeof(S));
+        pipe.ring = smem + Ly.ring;
+        pipe.stride = Ly.tile_bytes;
+        c.pipe = pipe;
+        if (threadIdx.x == 0) pipe_err_s = 0;
         c.vpart = (double*)(smem + Ly.vpart);
         c.vout = (double*)(smem + Ly.vout);
         c.spart = (double*)(smem + Ly.spart);
@@ -852,7 +1049,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             double rA = 0, pin = 0, nAx = 0, nCl = 0;
             for (int p0 = 0; p0 < P; p0 += kPC) {
                 const int pc = min(kPC, P - p0);
-                reduce_chunk<PCMAX>(c, p0, pc, c.I.xb, c.I.xn, c.I.xn, check ? c.I.xb : (const double*)nullptr, true);
+                reduce_chunk<PCMAX>(c, p0, pc, c.I.xb, c.I.xn, c.I.xn, (const double*)nullptr, true);
                 team_reduce<false>(cl, c.vpart, c.vout, pc * Lr, G, g);
                 for (int e = c.tid; e < pc * m; e += kThreads) {
                     const int q = e / m, jj = e % m;
@@ -880,9 +1077,20 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                 for (int e = c.tid; e < pc * k; e += kThreads) {
                     const int q = e / k, jj = e % k;
                     c.u[(p0 + q) * k + jj] = c.vout[q * Lr + 2 * m + jj];
-                    if (check) c.ub[(p0 + q) * k + jj] = c.vout[q * Lr + 2 * m + k + jj];
                 }
                 __syncthreads();
+                if (check) {
+                    // F^T (x_bar - c) for the KKT check in FP64 products: the objective
+                    // term kappa u^T Omega u must not carry the FP32 product error
+                    reduce_chunk<PCMAX, double>(c, p0, pc, (const double*)nullptr, (const double*)nullptr,
+                                                (const double*)nullptr, c.I.xb, true);
+                    team_reduce<false>(cl, c.vpart, c.vout, pc * Lr, G, g);
+                    for (int e = c.tid; e < pc * k; e += kThreads) {
+                        const int q = e / k, jj = e % k;
+                        c.ub[(p0 + q) * k + jj] = c.vout[q * Lr + 2 * m + k + jj];
+                    }
+                    __syncthreads();
+                }
             }
             // rotate iterate buffers: x <- x_new, y_D <- y_D new
             {
@@ -928,7 +1136,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                     __syncthreads();
                 }
             }
-            double kloc[7] = {0, 0, 0, 0, 0, 0, 0};
+            double kloc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
             {
                 const double* xb = c.I.xb;
                 const double* ydb = c.I.yDb;
@@ -945,6 +1153,8 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                     kloc[2] += xv * xv;
                     kloc[3] += gf * gf;
                     kloc[4] += kt * kt;
+                    kloc[7] += kap * c.I.Dp[o] * dx * dx;                        // specific risk
+                    kloc[8] += fabs(c.I.alpha[o] * xv);                          // return magnitudes
                 });
                 // trade costs phi(Delta x_bar + b) and h_D*(yD_bar) = -<y, b> + sum phi*(y)
                 for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
@@ -965,13 +1175,17 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                     }
                 }
             }
-            double part[9] = {rloc[0], rloc[1], kloc[0], kloc[1], kloc[2], kloc[3], kloc[4], kloc[5], kloc[6]};
-            block_reduce<9>(part, c.spart, c.wred, c.lane, c.warp);
-            if (c.tid == 0) c.spart[9] = (g == 0) ? (double)(globaltimer() - t_start) : 0.0;
+            double part[11] = {rloc[0], rloc[1], kloc[0], kloc[1], kloc[2], kloc[3],
+                               kloc[4], kloc[5], kloc[6], kloc[7], kloc[8]};
+            block_reduce<11>(part, c.spart, c.wred, c.lane, c.warp);
+            if (c.tid == 0) {
+                c.spart[11] = (g == 0) ? (double)(globaltimer() - t_start) : 0.0;
+                c.spart[12] = (double)pipe_err_s;
+            }
             __syncthreads();
-            team_reduce<false>(cl, c.spart, c.sout, 10, G, g);
-            double sums[10];
-            for (int e = 0; e < 10; ++e) sums[e] = c.sout[e];
+            team_reduce<false>(cl, c.spart, c.sout, 13, G, g);
+            double sums[13];
+            for (int e = 0; e < 13; ++e) sums[e] = c.sout[e];
             __syncthreads();
             // per-period max_i |grad f + K^T y| = |x_bar - q|   (g*(-grad f - K^T y))
             for (int p = 0; p < P; ++p) {
@@ -1016,20 +1230,30 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             const double Dobj = fval - sums[3] - gstar - hA - sums[8];
             const double r_p = sqrt(pin_t) / (sqrt(nAx_t) + sqrt(nCl_t) + 1e-30);
             const double r_d = rd_num / (sqrt(sums[4]) + sqrt(sums[5]) + sqrt(sums[6]) + 1e-30);
-            const double r_g = fabs(Pobj - Dobj) / (fabs(Pobj) + fabs(Dobj) + 1e-30);
+            // gap relative to the larger of |P| + |D| and the magnitude of the
+            // objective's terms (return magnitudes + risk + trading cost), so that
+            // an optimal value that nearly cancels does not demand more precision
+            // than the terms are computed with
+            const double phi_terms = sums[10] + sums[9] + kap * fF_t + sums[7];
+            const double r_g = fabs(Pobj - Dobj) / (fmax(fabs(Pobj) + fabs(Dobj), phi_terms) + 1e-30);
             const double rel = fmax(r_p, fmax(r_d, r_g));
             const double fpr = sqrt(sums[0] / tau + sums[1] / sD + rA_t / sA);
             res_rel = rel; res_p = r_p; res_d = r_d; res_g = r_g; res_P = Pobj; res_D = Dobj;
             r_last = fpr;
             lap(5);
+            if (sums[12] > 0) { status = FF_STALLED; break; }
             if (!(rel == rel) || !(fpr == fpr)) { status = FF_NUMERICAL; break; }
             if (rel <= prm.tol) { status = FF_CONVERGED; break; }
-            if (sums[9] > prm.time_limit_ns) { status = FF_TIME_LIMIT; break; }
+            if (sums[11] > prm.time_limit_ns) { status = FF_TIME_LIMIT; break; }
             // restart on the fixed-point residual (sufficient / necessary decay);
             // the anchor becomes the current iterate
             if (r_restart < 0) r_restart = fpr;
-            const bool do_restart =
-                (fpr <= prm.beta_suff * r_restart) || (fpr <= prm.beta_nec * r_restart && fpr > r_prev);
+            // restart on sufficient decay, on necessary decay that stalls, or
+            // (artificial) once the current restart cycle holds a fixed share
+            // of all iterations so far
+            const bool do_restart = (fpr <= prm.beta_suff * r_restart) ||
+                                    (fpr <= prm.beta_nec * r_restart && fpr > r_prev) ||
+                                    (prm.beta_art > 0 && (double)j >= prm.beta_art * (double)(it + 1));
             r_prev = fpr;
             if (do_restart) {
                 for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
@@ -1087,8 +1311,17 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             for (int q = 0; q < 6; ++q) rs.phase_seconds[q] = ph[q] * 1e-9;
             *c.I.res = rs;
         }
+        pipe = c.pipe;
         // the next instance reuses shared memory: every rank must be done with it
         cl.sync();
+    }
+    // a copy whose wait expired may still be landing: give it (bounded) time
+    // before the CTA's shared memory is released
+    if (pipe_err_s) {
+        for (int s2 = 0; s2 < kStages; ++s2) {
+            pipe.head = s2;
+            pipe_wait(pipe);
+        }
     }
 }
 

@@ -79,4 +79,4 @@ def test_batch_plan_groups_by_cluster_size(lib):
     assert cl[-1] == 16 and nl == 2          # 29 * 3500 asset-periods > 8 * 8192
     o.cluster_size = 4
     cl, nl = _lib.ff_batch_plan(st, len(probs), o)
-    assert set(cl) == {4} and nl == 1
+    assert set(cl) == {4} and nl == 2          # one launch per kind: single- and multi-period

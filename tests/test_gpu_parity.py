@@ -1,7 +1,7 @@
 """GPU parity: the CUDA solver against the FP64 oracle on the same seeded inputs.
 
-Bar (per instance): status converged at relative KKT <= 1e-6 (the solver's own
-FP64 reductions), |w - w*|_inf <= 1e-5, relative objective gap <= 1e-6 with the
+Bar (per instance): status converged (solved to TOL_SOLVE = 2e-7, see below), relative
+KKT <= 1e-6 (the solver's own FP64 reductions), |w - w*|_inf <= 1e-5, relative objective gap <= 1e-6 with the
 objective of the GPU's w evaluated by the oracle, and the oracle's own
 evaluation of the relative KKT at the GPU's (w, y) <= 3e-6 (the returned
 iterate is rounded to the storage precision).
@@ -26,6 +26,10 @@ pytestmark = pytest.mark.gpu
 TOL_W = 1e-5
 TOL_OBJ = 1e-6
 TOL_KKT = 1e-6
+# The solves run to 2e-7 relative KKT: a point at 1e-6 relative KKT is only
+# guaranteed within sqrt(2 gap / mu) of the optimum (mu = 2 kappa min D), which
+# can exceed the 1e-5 bar on |w - w*|_inf; the tighter stop meets both bars.
+TOL_SOLVE = 2e-7
 
 
 @pytest.fixture(scope="module")
@@ -70,14 +74,14 @@ def _compare(prob_rounded, sol, ref=None, kkt_slack=3.0):
 def test_single_small_config(api, precision):
     prob = S.config_single_small()
     pr = prob if precision == "f64" else prob.rounded(np.float32)
-    sol = api.solve(pr, precision=precision, return_duals=True)
+    sol = api.solve(pr, precision=precision, return_duals=True, tol=TOL_SOLVE)
     _compare(pr, sol)
 
 
 @pytest.mark.parametrize("n,k,seed", [(1, 1, 1), (33, 3, 2), (97, 5, 3), (1000, 24, 4), (2049, 16, 5)])
 def test_single_ragged(api, n, k, seed):
     prob = S.make_single(n, k, seed, n_onehot=max(1, k // 3)).rounded(np.float32)
-    sol = api.solve(prob, precision="f32", return_duals=True)
+    sol = api.solve(prob, precision="f32", return_duals=True, tol=TOL_SOLVE)
     _compare(prob, sol)
 
 
@@ -86,7 +90,7 @@ def test_single_no_rows(api):
     prob.A = np.zeros((0, prob.n))
     prob.L = np.zeros(0)
     prob.U = np.zeros(0)
-    sol = api.solve(prob, precision="f64", return_duals=True)
+    sol = api.solve(prob, precision="f64", return_duals=True, tol=TOL_SOLVE)
     _compare(prob, sol)
 
 
@@ -94,14 +98,14 @@ def test_single_no_rows(api):
 def test_multi_small(api, T, n, k, prec):
     prob = S.make_multi(T, n, k, 20 + T, n_onehot=max(1, k // 3))
     pr = prob if prec == "f64" else prob.rounded(np.float32)
-    sol = api.solve(pr, precision=prec, return_duals=True)
+    sol = api.solve(pr, precision=prec, return_duals=True, tol=TOL_SOLVE)
     _compare(pr, sol)
 
 
 @pytest.mark.parametrize("G", [1, 2, 4, 8, 16])
 def test_cluster_sizes_agree(api, G):
     prob = S.make_single(3000, 20, 9, n_onehot=5).rounded(np.float32)
-    sol = api.solve(prob, precision="f32", return_duals=True, cluster_size=G)
+    sol = api.solve(prob, precision="f32", return_duals=True, cluster_size=G, tol=TOL_SOLVE)
     _compare(prob, sol)
 
 
@@ -110,7 +114,7 @@ def test_batch_bf16_mixed(api):
              enumerate([(500, 40), (1733, 80), (64, 40), (2500, 40)])]
     probs += [S.make_multi(T, n, k, 200 + i).with_F_rounded_bf16() for i, (T, n, k) in
               enumerate([(5, 400, 40), (9, 1000, 80)])]
-    ws, infos = api.solve_batch(probs, precision="bf16")
+    ws, infos = api.solve_batch(probs, precision="bf16", tol=TOL_SOLVE)
     for p, w, info in zip(probs, ws, infos):
         class _S:  # adapter with the Solution interface
             pass
@@ -128,7 +132,7 @@ def test_batch_graph_replay_matches_direct_call(api):
     import torch
     probs = [S.make_single(n, 40, 300 + i) for i, n in enumerate([900, 2600, 150])]
     probs += [S.make_multi(6, 500, 40, 310)]
-    br = api.BatchRunner(probs, precision="bf16")
+    br = api.BatchRunner(probs, precision="bf16", tol=TOL_SOLVE)
     br.run()
     torch.cuda.synchronize()
     w_direct = [w.copy() for w in br.portfolios()]
