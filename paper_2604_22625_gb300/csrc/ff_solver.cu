@@ -117,10 +117,12 @@ size_t solver_smem_bytes(int P, int k, int m, int omega_diag, size_t matvec_size
 
 int choose_tile(int P, int k, int m, int omega_diag, size_t matvec_size, size_t panel_size) {
     const int Rp = (k + 7) / 8 * 8 + (m + 7) / 8 * 8;
+    // the single-period variant is built for kSingleCtasPerSm resident CTAs
+    const size_t limit = P == 1 ? (size_t)kSmemLimit / kSingleCtasPerSm - 1024 : (size_t)kSmemLimit;
+    const size_t max_tile = P == 1 ? (size_t)kMaxTileBytes / kSingleCtasPerSm : (size_t)kMaxTileBytes;
     for (int CH = 256; CH >= 8; CH /= 2) {
-        if ((size_t)Rp * CH * panel_size > (size_t)kMaxTileBytes) continue;
-        if (make_layout(P, k, m, omega_diag, matvec_size, CH, Rp, panel_size).total <= (size_t)kSmemLimit)
-            return CH;
+        if ((size_t)Rp * CH * panel_size > max_tile) continue;
+        if (make_layout(P, k, m, omega_diag, matvec_size, CH, Rp, panel_size).total <= limit) return CH;
     }
     return 0;
 }
