@@ -225,6 +225,44 @@ int ff_batch_plan(const ff_problem* probs, int count, const ff_options* o, int32
 /* Message for an FF_* return code (static storage). */
 const char* ff_status_string(int code);
 
+/* Gradient outputs of ff_backward_single: DEVICE pointers with the layout and
+ * element type of the matching ff_problem arrays (alpha, D, s, q, w0: n
+ * entries; F: n x k row-major).  Any may be NULL (not computed). */
+typedef struct ff_grads {
+    void* alpha;
+    void* F;
+    void* D;
+    void* s;
+    void* q;
+    void* w0;
+} ff_grads;
+
+/* Workspace bytes of ff_backward_single for this problem (host only; 0 if p
+ * is invalid or multi-period). */
+size_t ff_backward_workspace_size(const ff_problem* p);
+
+/* Vector-Jacobian product of the single-period solve (Sec. 2.1, Eqs. 1-3):
+ * with L = <grad_w, w*>, writes dL/dalpha, dL/dF, dL/dD, dL/ds, dL/dq and
+ * dL/dw0 (paper units: alpha, F, D, s, q, w0 as passed in p) to `out`.
+ * Implicit differentiation of the optimality conditions at w*: the active
+ * structure is read from the forward results (zero holdings: w_i == 0; dead
+ * trades: |yD_i| < lambda2 s_i; active exposure rows: |yA_j| > 1e-12 max|yA|;
+ * active budget: ||w||_1 >= 1 - 1e-10 for FP64 data, 1 - 1e-6 for FP32), and
+ * the reduced KKT system is solved
+ * in FP64 on the GPU (Woodbury through the k x k factor block, Schur
+ * complement on the active constraints).  A is treated as independent data
+ * (no derivative through A).  At a point where a piece is exactly on its
+ * kink boundary the result is the one-sided derivative of the identified
+ * active set.
+ *   w, yA, yD  : device, the forward outputs of ff_solve_single (n, m, n
+ *                entries of p->dtype; yA may be NULL when m = 0).
+ *   grad_w     : device, n entries of p->dtype.
+ *   status_dev : device int32 or NULL: 0 ok, 1 / 2 a factorisation met a
+ *                non-positive pivot (degenerate active set).
+ * Asynchronous on `stream`; FF_OK or an FF_ERR_* code. */
+int ff_backward_single(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,
+                       const ff_grads* out, void* ws, size_t ws_bytes, int32_t* status_dev, void* stream);
+
 /* Description of the CUDA runtime call that made the last FF_ERR_CUDA return
  * on the calling host thread ("" if none); static thread-local storage. */
 const char* ff_last_error(void);

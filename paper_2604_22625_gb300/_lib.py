@@ -59,6 +59,11 @@ class ff_options(C.Structure):
                 ("restart_artificial", C.c_double)]
 
 
+class ff_grads(C.Structure):
+    _fields_ = [("alpha", C.c_void_p), ("F", C.c_void_p), ("D", C.c_void_p), ("s", C.c_void_p),
+                ("q", C.c_void_p), ("w0", C.c_void_p)]
+
+
 class ff_result(C.Structure):
     _fields_ = [("status", C.c_int32), ("restarts", C.c_int32), ("iterations", C.c_int64),
                 ("rel_kkt", C.c_double), ("r_primal", C.c_double), ("r_dual", C.c_double),
@@ -75,7 +80,7 @@ assert RESULT_DTYPE.itemsize == C.sizeof(ff_result)
 
 EXPORTS = ("ff_default_options", "ff_workspace_size", "ff_solve_single", "ff_solve_multi",
            "ff_solve_batch", "ff_status_string", "ff_version", "ff_last_error",
-           "ff_solve_single_static", "ff_batch_plan")
+           "ff_solve_single_static", "ff_batch_plan", "ff_backward_single", "ff_backward_workspace_size")
 
 _lib = None
 
@@ -97,6 +102,11 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     for name in ("ff_solve_single", "ff_solve_multi"):
         getattr(lib, name).argtypes = sig
         getattr(lib, name).restype = C.c_int
+    lib.ff_backward_workspace_size.argtypes = [C.POINTER(ff_problem)]
+    lib.ff_backward_workspace_size.restype = C.c_size_t
+    lib.ff_backward_single.argtypes = [C.POINTER(ff_problem), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.POINTER(ff_grads), C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]
+    lib.ff_backward_single.restype = C.c_int
     lib.ff_batch_plan.argtypes = [C.POINTER(ff_problem), C.c_int, C.POINTER(ff_options),
                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.ff_batch_plan.restype = C.c_int
@@ -147,6 +157,17 @@ def ff_solve_single_static(prob: ff_problem, opts: ff_options, res: int, w: int,
     return int(load().ff_solve_single_static(C.byref(prob), C.byref(opts), C.c_void_p(res), C.c_void_p(w),
                                              C.c_void_p(yA or None), C.c_void_p(yD or None),
                                              C.c_void_p(stream or None)))
+
+
+def ff_backward_workspace_size(prob: ff_problem) -> int:
+    return int(load().ff_backward_workspace_size(C.byref(prob)))
+
+
+def ff_backward_single(prob: ff_problem, w: int, yA: int, yD: int, grad_w: int, grads: ff_grads, ws: int,
+                       ws_bytes: int, status: int = 0, stream: int = 0) -> int:
+    return int(load().ff_backward_single(C.byref(prob), C.c_void_p(w), C.c_void_p(yA or None), C.c_void_p(yD),
+                                         C.c_void_p(grad_w), C.byref(grads), C.c_void_p(ws), ws_bytes,
+                                         C.c_void_p(status or None), C.c_void_p(stream or None)))
 
 
 def ff_batch_plan(probs, count: int, opts: ff_options):
