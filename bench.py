@@ -48,7 +48,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "single_large", "multi", "single_small", "batch_profile"])
+                    choices=["batch", "single_large", "multi", "single_small", "batch_profile", "diff"])
     ap.add_argument("--max-iter", type=int, default=0, help="iteration cap (profiling runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="call ff_solve_batch directly instead of "
@@ -73,6 +73,11 @@ def make_workload(name: str, rank: int):
     if name == "batch_profile":
         probs = [p for p in S.config_batch(seed=3 + 10 * rank, n_single=152, n_multi=0)]
         return probs, "bf16", "profiling case: 152 single-period instances of the batched workload"
+    if name == "diff":
+        probs = S.config_diff(seed=4 + 10 * rank, n_single=64, n_multi=0)
+        return probs, "f32", ("differentiation: 64 single-period instances n=3000 k=60, forward to 1e-7 "
+                              "relative KKT then the batched adjoint (vector-Jacobian products for alpha, F, D, "
+                              "s, q, w0)")
     if name == "single_large":
         return [S.config_single_large(seed=1 + 10 * rank)], "f32", "single-period n=10000 k=100 m=160, FP32"
     if name == "multi":
@@ -315,15 +320,28 @@ def run_ours(args):
     opt_kw = {"time_limit": 600.0}
     if args.max_iter > 0:
         opt_kw["max_iter"] = args.max_iter
-    runner = api.BatchRunner(probs, precision=precision, device=str(dev), **opt_kw)
+    diff = args.workload == "diff"
+    if diff:
+        opt_kw["tol"] = 1e-7
+    runner = api.BatchRunner(probs, precision=precision, device=str(dev), duals=diff, **opt_kw)
+    tol_ok = 1e-7 if diff else TOL
+    if diff:
+        runner.prepare_backward()
+        gen = torch.Generator(device="cpu").manual_seed(4)
+        runner.g_dev.copy_(torch.randn(runner.g_dev.shape, generator=gen, dtype=runner.g_dev.dtype))
     stream = torch.cuda.current_stream(dev)
     bpi = [algorithmic_bytes_per_iter(p, precision) for p in probs]
     resident_in = runner.h2d_bytes
 
-    use_graph = not args.no_graph
+    use_graph = not args.no_graph and not diff
     if use_graph:
         runner.capture(stream)
-    step = runner.replay if use_graph else runner.run
+    if diff:
+        def step(s_):
+            runner.run(s_)
+            runner.backward(s_)
+    else:
+        step = runner.replay if use_graph else runner.run
     for _ in range(args.warmup):
         step(stream)
     torch.cuda.synchronize(dev)
@@ -348,13 +366,13 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     dev_s = sum(step_ms) / 1e3
     infos = runner.results()   # the last step's results (every step solves the same inputs)
-    solved = sum(1 for i in infos if i["status"] == 0 and i["rel_kkt"] <= TOL)
+    solved = sum(1 for i in infos if i["status"] == 0 and i["rel_kkt"] <= tol_ok)
     kkt_max = max(i["rel_kkt"] for i in infos)
     iters = [int(i["iterations"]) for i in infos]
     inst_s = [float(i["seconds"]) for i in infos]
     alg_bytes = float(sum(b * it for b, it in zip(bpi, iters)))
 
-    launches_per_step = 1 + runner.solver_launches()
+    launches_per_step = 1 + runner.solver_launches() + (1 if diff else 0)
     t_max = max_over_ranks(dist, dev_s, dev)
     solved_all = sum_over_ranks(dist, float(solved * args.steps), dev)
     value = solved_all / t_max if t_max > 0 else 0.0
@@ -372,7 +390,7 @@ def run_ours(args):
 
     # end to end through the public API: pinned host inputs -> solve -> host results
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not diff:
         k_e2e = 1
         if dist is not None:
             dist.barrier()
@@ -410,7 +428,7 @@ def run_ours(args):
                            f"({ns} mean_single + {nm} mean_multi) of device seconds"}
 
     cpu = None
-    if not args.no_cpu and rank == 0 and ws == 1:
+    if not args.no_cpu and rank == 0 and ws == 1 and not diff:
         rate, sample, spent, ts, tm = oracle_sample_rate(probs, precision, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample}
 
@@ -422,7 +440,7 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"bf16": "bf16", "f32": "f32", "f64": "f64"}[precision],
             "data": "synthetic",
-            "config": {"workload": desc, "instances": len(probs), "tol": TOL,
+            "config": {"workload": desc, "instances": len(probs), "tol": tol_ok,
                        "precision": {"bf16": "BF16 F/A panels, FP32 matvecs, FP64 iterate state and KKT",
                                      "f32": "FP32 panels and matvecs, FP64 iterate state and KKT",
                                      "f64": "FP64 throughout"}[precision],

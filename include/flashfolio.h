@@ -175,9 +175,12 @@ int ff_solve_multi(const ff_problem* p, const ff_options* o, void* ws, size_t ws
 /* Solve `count` independent instances (single- and multi-period mixed) in one
  * persistent launch.  probs is a HOST array of count problems (1 <= count <=
  * 65535); w_out is a HOST array of count DEVICE pointers (layout as above);
+ * yA_out and yD_out are NULL or HOST arrays of count DEVICE pointers (entries
+ * may be NULL) receiving the multipliers as in ff_solve_single/multi;
  * result_dev is a device array of count ff_result. */
 int ff_solve_batch(const ff_problem* probs, int count, const ff_options* o, void* ws, size_t ws_bytes,
-                   ff_result* result_dev, void* const* w_out, void* stream);
+                   ff_result* result_dev, void* const* w_out, void* const* yA_out, void* const* yD_out,
+                   void* stream);
 
 /* Size of the library-owned workspace used by ff_solve_single_static (32 MiB). */
 #define FF_STATIC_WORKSPACE_BYTES (32u * 1024u * 1024u)
@@ -262,6 +265,16 @@ size_t ff_backward_workspace_size(const ff_problem* p);
  * Asynchronous on `stream`; FF_OK or an FF_ERR_* code. */
 int ff_backward_single(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,
                        const ff_grads* out, void* ws, size_t ws_bytes, int32_t* status_dev, void* stream);
+
+/* ff_backward_single for `count` single-period instances in one launch (one
+ * CTA per instance).  probs, w, yA, yD, grad_w and out are HOST arrays of
+ * count entries (pointers inside are DEVICE pointers as in
+ * ff_backward_single; yA may be NULL when every m = 0); status_dev is NULL
+ * or a device array of count int32.  Workspace: ff_backward_batch_workspace_size. */
+size_t ff_backward_batch_workspace_size(const ff_problem* probs, int count);
+int ff_backward_batch(const ff_problem* probs, int count, const void* const* w, const void* const* yA,
+                      const void* const* yD, const void* const* grad_w, const ff_grads* out, void* ws,
+                      size_t ws_bytes, int32_t* status_dev, void* stream);
 
 /* Description of the CUDA runtime call that made the last FF_ERR_CUDA return
  * on the calling host thread ("" if none); static thread-local storage. */

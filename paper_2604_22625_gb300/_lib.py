@@ -80,7 +80,8 @@ assert RESULT_DTYPE.itemsize == C.sizeof(ff_result)
 
 EXPORTS = ("ff_default_options", "ff_workspace_size", "ff_solve_single", "ff_solve_multi",
            "ff_solve_batch", "ff_status_string", "ff_version", "ff_last_error",
-           "ff_solve_single_static", "ff_batch_plan", "ff_backward_single", "ff_backward_workspace_size")
+           "ff_solve_single_static", "ff_batch_plan", "ff_backward_single", "ff_backward_workspace_size",
+           "ff_backward_batch", "ff_backward_batch_workspace_size")
 
 _lib = None
 
@@ -107,6 +108,12 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.ff_backward_single.argtypes = [C.POINTER(ff_problem), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.POINTER(ff_grads), C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]
     lib.ff_backward_single.restype = C.c_int
+    lib.ff_backward_batch_workspace_size.argtypes = [C.POINTER(ff_problem), C.c_int]
+    lib.ff_backward_batch_workspace_size.restype = C.c_size_t
+    vp = C.POINTER(C.c_void_p)
+    lib.ff_backward_batch.argtypes = [C.POINTER(ff_problem), C.c_int, vp, vp, vp, vp, C.POINTER(ff_grads),
+                                      C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]
+    lib.ff_backward_batch.restype = C.c_int
     lib.ff_batch_plan.argtypes = [C.POINTER(ff_problem), C.c_int, C.POINTER(ff_options),
                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.ff_batch_plan.restype = C.c_int
@@ -114,7 +121,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.ff_solve_single_static.restype = C.c_int
     lib.ff_solve_batch.argtypes = [C.POINTER(ff_problem), C.c_int, C.POINTER(ff_options), C.c_void_p,
-                                   C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p), C.c_void_p]
+                                   C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                   C.POINTER(C.c_void_p), C.c_void_p]
     lib.ff_solve_batch.restype = C.c_int
     lib.ff_status_string.argtypes = [C.c_int]
     lib.ff_status_string.restype = C.c_char_p
@@ -181,10 +189,26 @@ def ff_batch_plan(probs, count: int, opts: ff_options):
 
 
 def ff_solve_batch(probs, count: int, opts: ff_options, ws: int, ws_bytes: int, res: int, w_ptrs,
-                   stream: int = 0) -> int:
+                   stream: int = 0, yA_ptrs=None, yD_ptrs=None) -> int:
     arr = (C.c_void_p * count)(*w_ptrs)
+    ya = (C.c_void_p * count)(*yA_ptrs) if yA_ptrs is not None else None
+    yd = (C.c_void_p * count)(*yD_ptrs) if yD_ptrs is not None else None
     return int(load().ff_solve_batch(probs, count, C.byref(opts), C.c_void_p(ws), ws_bytes, C.c_void_p(res),
-                                     arr, C.c_void_p(stream or None)))
+                                     arr, ya, yd, C.c_void_p(stream or None)))
+
+
+def ff_backward_batch_workspace_size(probs, count: int) -> int:
+    return int(load().ff_backward_batch_workspace_size(probs, count))
+
+
+def ff_backward_batch(probs, count: int, w_ptrs, yA_ptrs, yD_ptrs, g_ptrs, grads, ws: int, ws_bytes: int,
+                      status: int = 0, stream: int = 0) -> int:
+    def arr(v):
+        return (C.c_void_p * count)(*v) if v is not None else None
+    gr = (ff_grads * count)(*grads)
+    return int(load().ff_backward_batch(probs, count, arr(w_ptrs), arr(yA_ptrs), arr(yD_ptrs), arr(g_ptrs), gr,
+                                        C.c_void_p(ws), ws_bytes, C.c_void_p(status or None),
+                                        C.c_void_p(stream or None)))
 
 
 def ff_status_string(code: int) -> str:

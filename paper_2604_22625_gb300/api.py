@@ -187,7 +187,8 @@ class BatchRunner:
     from pinned host memory, the solve, and one copy of the portfolios and
     results back to pinned host memory, all on one stream."""
 
-    def __init__(self, problems: Sequence, precision: str = "bf16", device: str = "cuda", **opt_kw):
+    def __init__(self, problems: Sequence, precision: str = "bf16", device: str = "cuda", duals: bool = False,
+                 **opt_kw):
         self.precision = precision
         self.device = torch.device(device)
         self.dtype = torch.float64 if precision == "f64" else torch.float32
@@ -215,6 +216,18 @@ class BatchRunner:
         self.w_dev = torch.empty(int(self.w_off[-1]), dtype=self.dtype, device=self.device)
         welem = self.w_dev.element_size()
         self.w_ptrs = [self.w_dev.data_ptr() + int(o) * welem for o in self.w_off[:-1]]
+        self.yA_ptrs = self.yD_ptrs = None
+        if duals:
+            m_ = [int(np.asarray(p.A).shape[0]) for p in self.problems]
+            R_ = [int(p.T) if int(p.T) >= 2 else 1 for p in self.problems]
+            self.yA_off = np.concatenate([[0], np.cumsum([(P * m + _ALIGN) // _ALIGN * _ALIGN
+                                                          for P, m in zip(self.P, m_)])]).astype(np.int64)
+            self.yD_off = np.concatenate([[0], np.cumsum([(R * n + _ALIGN - 1) // _ALIGN * _ALIGN
+                                                          for R, n in zip(R_, self.n)])]).astype(np.int64)
+            self.yA_dev = torch.zeros(int(self.yA_off[-1]), dtype=self.dtype, device=self.device)
+            self.yD_dev = torch.zeros(int(self.yD_off[-1]), dtype=self.dtype, device=self.device)
+            self.yA_ptrs = [self.yA_dev.data_ptr() + int(o) * welem for o in self.yA_off[:-1]]
+            self.yD_ptrs = [self.yD_dev.data_ptr() + int(o) * welem for o in self.yD_off[:-1]]
         pin = torch.cuda.is_available()
         self.w_host = torch.empty(self.w_dev.shape, dtype=self.dtype, pin_memory=pin)
         self.res_host = torch.empty(self.res.shape, dtype=torch.uint8, pin_memory=pin)
@@ -238,7 +251,7 @@ class BatchRunner:
     def run(self, stream: Optional[torch.cuda.Stream] = None) -> None:
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         rc = L.ff_solve_batch(self.structs, self.count, self.opts, self.ws.data_ptr(), self.ws_bytes,
-                              self.res.data_ptr(), self.w_ptrs, s.cuda_stream)
+                              self.res.data_ptr(), self.w_ptrs, s.cuda_stream, self.yA_ptrs, self.yD_ptrs)
         if rc != L.FF_OK:
             raise RuntimeError(f"batch solve failed: {L.ff_status_string(rc)} ({rc}) {L.ff_last_error()}")
 
@@ -280,6 +293,45 @@ class BatchRunner:
                 self.run(s)
             self.w_host.copy_(self.w_dev, non_blocking=True)
             self.res_host.copy_(self.res, non_blocking=True)
+
+    def prepare_backward(self) -> None:
+        """Buffers of the batched adjoint (single-period instances, duals on):
+        ``g_dev`` holds the upstream gradients in the portfolio layout,
+        ``grad_dev`` the gradients of alpha, F, D, s, q, w0 in the packed
+        input layout (``layout``)."""
+        if self.yD_ptrs is None:
+            raise ValueError("BatchRunner(duals=True) is needed for the adjoint")
+        if any(int(p.T) >= 2 for p in self.problems):
+            raise ValueError("the adjoint covers single-period instances")
+        self.g_dev = torch.zeros_like(self.w_dev)
+        self.grad_dev = torch.zeros_like(self.dev_in)
+        elem = self.grad_dev.element_size()
+        base = self.grad_dev.data_ptr()
+        welem = self.w_dev.element_size()
+        self.g_ptrs = [self.g_dev.data_ptr() + int(o) * welem for o in self.w_off[:-1]]
+        self.grads = []
+        for ent in self.layout:
+            gr = L.ff_grads()
+            for nm in ("alpha", "F", "D", "s", "q", "w0"):
+                setattr(gr, nm, base + ent[nm][0] * elem)
+            self.grads.append(gr)
+        self.bws_bytes = L.ff_backward_batch_workspace_size(self.structs, self.count)
+        self.bws = torch.empty(self.bws_bytes, dtype=torch.uint8, device=self.device)
+        self.bstatus = torch.zeros(self.count, dtype=torch.int32, device=self.device)
+
+    def backward(self, stream: Optional[torch.cuda.Stream] = None) -> None:
+        """Vector-Jacobian products of every instance for the gradients in g_dev."""
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        rc = L.ff_backward_batch(self.structs, self.count, self.w_ptrs, self.yA_ptrs, self.yD_ptrs, self.g_ptrs,
+                                 self.grads, self.bws.data_ptr(), self.bws_bytes, self.bstatus.data_ptr(),
+                                 s.cuda_stream)
+        if rc != L.FF_OK:
+            raise RuntimeError(f"backward failed: {L.ff_status_string(rc)} ({rc}) {L.ff_last_error()}")
+
+    def gradient(self, i: int, name: str) -> np.ndarray:
+        off, size = self.layout[i][name]
+        a = self.grad_dev[off:off + size].cpu().numpy().astype(np.float64)
+        return a.reshape(np.shape(getattr(self.problems[i], name)))
 
     def results(self) -> List[dict]:
         recs = self.res.cpu().numpy().view(L.RESULT_DTYPE)

@@ -52,6 +52,7 @@ struct AdjInst {
     double* vr;          // 4 (m + 2): E diag(1/h) g, nu, scratch
     double* vk;          // 6 k: F^T x, F^T u, Omega F^T x, Omega F^T u, t, scratch
     int* flags;          // [0] number of active constraints, [1] status
+    int32_t* status_out; // device or null: the instance's status
 };
 
 __device__ __forceinline__ double ld(const void* p, size_t i, int f64) {
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_single_kernel(const AdjIn
         for (int e = tid; e < k * k; e += kAdjThreads) I.Oi[e] = 2.0 * kap * ld(I.Omega, e, f64);
         __syncthreads();
         if (!cholesky(I.Oi, k, k, &sflag)) {
-            if (tid == 0) I.flags[1] = 1;
+            if (tid == 0) { I.flags[1] = 1; if (I.status_out) *I.status_out = 1; }
             return;
         }
         for (int c = 0; c < k; ++c) {
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_single_kernel(const AdjIn
         for (int a = tid; a < r; a += kAdjThreads) nu[a] = I.vr[a];
         __syncthreads();
         if (!cholesky(I.Sc, r, lds, &sflag)) {
-            if (tid == 0) I.flags[1] = 2;
+            if (tid == 0) { I.flags[1] = 2; if (I.status_out) *I.status_out = 2; }
             return;
         }
         chol_solve(I.Sc, r, lds, nu, 1, 1);
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_single_kernel(const AdjIn
             for (int j = 0; j < k; ++j) st(I.dF, (size_t)i * k + j, -2.0 * kap * (uu * OFtx[j] + x * OFtu[j]), f64);
         }
     }
-    if (tid == 0) I.flags[1] = 0;
+    if (tid == 0) { I.flags[1] = 0; if (I.status_out) *I.status_out = 0; }
 }
 
 inline size_t a256(size_t x) { return (x + 255) / 256 * 256; }
@@ -370,23 +371,22 @@ size_t adj_bytes(int n, int k, int m) {
 }  // namespace
 }  // namespace ff
 
-extern "C" {
+namespace ff {
+namespace {
 
-size_t ff_backward_workspace_size(const ff_problem* p) {
-    if (!p || p->T != 0 || p->n < 1 || p->k < 1 || p->m < 0) return 0;
-    return ff::a256(sizeof(ff::AdjInst)) + ff::adj_bytes(p->n, p->k, p->m);
+bool valid_backward(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,
+                    const ff_grads* out) {
+    if (!p || p->T != 0 || !w || !yD || !grad_w || !out) return false;
+    if (p->n < 1 || p->k < 1 || p->m < 0 || (p->m > 0 && (!yA || !p->A))) return false;
+    if (p->dtype != FF_F64 && p->dtype != FF_F32) return false;
+    if (!p->F || !p->Omega || !p->D || !p->alpha || !p->s || !p->q || !p->w0) return false;
+    if (!(p->GMV > 0) || !(p->lambda1 > 0) || !(p->d > 1.0 && p->d <= 2.0)) return false;
+    return true;
 }
 
-int ff_backward_single(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,
-                       const ff_grads* out, void* ws, size_t ws_bytes, int32_t* status_dev, void* stream) {
-    if (!p || p->T != 0 || !w || !yD || !grad_w || !out) return FF_ERR_INVALID_ARG;
-    if (p->n < 1 || p->k < 1 || p->m < 0 || (p->m > 0 && (!yA || !p->A))) return FF_ERR_INVALID_ARG;
-    if (p->dtype != FF_F64 && p->dtype != FF_F32) return FF_ERR_INVALID_ARG;
-    if (!p->F || !p->Omega || !p->D || !p->alpha || !p->s || !p->q || !p->w0) return FF_ERR_INVALID_ARG;
-    if (!(p->GMV > 0) || !(p->lambda1 > 0) || !(p->d > 1.0 && p->d <= 2.0)) return FF_ERR_INVALID_ARG;
-    const size_t need = ff_backward_workspace_size(p);
-    if (!ws || ((uintptr_t)ws % 256) != 0 || ws_bytes < need) return FF_ERR_WORKSPACE;
-    ff::AdjInst I;
+AdjInst carve_adj(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,
+                  const ff_grads* out, unsigned char*& cur, int32_t* status_out) {
+    AdjInst I;
     memset(&I, 0, sizeof(I));
     I.n = p->n; I.k = p->k; I.m = p->m; I.omega_diag = p->omega_diag ? 1 : 0; I.in_f64 = p->dtype == FF_F64;
     I.F = p->F; I.Omega = p->Omega; I.D = p->D; I.alpha = p->alpha; I.s = p->s; I.q = p->q; I.w0 = p->w0;
@@ -394,9 +394,7 @@ int ff_backward_single(const ff_problem* p, const void* w, const void* yA, const
     I.w = w; I.yA = yA; I.yD = yD; I.gw = grad_w;
     I.dalpha = out->alpha; I.dF = out->F; I.dD = out->D; I.ds = out->s; I.dq = out->q; I.dw0 = out->w0;
     I.kappa = p->lambda1 * p->GMV; I.lam2 = p->lambda2; I.lam3 = p->lambda3; I.d = p->d;
-    unsigned char* base = (unsigned char*)ws;
-    unsigned char* cur = base + ff::a256(sizeof(ff::AdjInst));
-    auto take = [&](size_t bytes) { unsigned char* r = cur; cur += ff::a256(bytes); return (void*)r; };
+    auto take = [&](size_t bytes) { unsigned char* r = cur; cur += a256(bytes); return (void*)r; };
     const int n = p->n, k = p->k, m = p->m;
     I.invh = (double*)take((size_t)n * 8);
     I.cls = (signed char*)take((size_t)n);
@@ -409,17 +407,64 @@ int ff_backward_single(const ff_problem* p, const void* w, const void* yA, const
     I.vr = (double*)take((size_t)4 * (m + 2) * 8);
     I.vk = (double*)take((size_t)6 * k * 8);
     I.flags = (int*)take(8);
+    I.status_out = status_out;
+    return I;
+}
+
+}  // namespace
+}  // namespace ff
+
+extern "C" {
+
+size_t ff_backward_workspace_size(const ff_problem* p) {
+    if (!p || p->T != 0 || p->n < 1 || p->k < 1 || p->m < 0) return 0;
+    return ff::a256(sizeof(ff::AdjInst)) + ff::adj_bytes(p->n, p->k, p->m);
+}
+
+size_t ff_backward_batch_workspace_size(const ff_problem* probs, int count) {
+    if (!probs || count < 1) return 0;
+    size_t b = ff::a256((size_t)count * sizeof(ff::AdjInst));
+    for (int t = 0; t < count; ++t) {
+        const ff_problem* p = &probs[t];
+        if (p->T != 0 || p->n < 1 || p->k < 1 || p->m < 0) return 0;
+        b += ff::adj_bytes(p->n, p->k, p->m);
+    }
+    return b;
+}
+
+int ff_backward_batch(const ff_problem* probs, int count, const void* const* w, const void* const* yA,
+                      const void* const* yD, const void* const* grad_w, const ff_grads* out, void* ws,
+                      size_t ws_bytes, int32_t* status_dev, void* stream) {
+    if (!probs || count < 1 || count > 65535 || !w || !yD || !grad_w || !out) return FF_ERR_INVALID_ARG;
+    for (int t = 0; t < count; ++t)
+        if (!ff::valid_backward(&probs[t], w[t], yA ? yA[t] : nullptr, yD[t], grad_w[t], &out[t]))
+            return FF_ERR_INVALID_ARG;
+    const size_t need = ff_backward_batch_workspace_size(probs, count);
+    if (!ws || ((uintptr_t)ws % 256) != 0 || ws_bytes < need) return FF_ERR_WORKSPACE;
+    unsigned char* base = (unsigned char*)ws;
+    unsigned char* cur = base + ff::a256((size_t)count * sizeof(ff::AdjInst));
+    std::vector<ff::AdjInst> table(count);
+    for (int t = 0; t < count; ++t)
+        table[t] = ff::carve_adj(&probs[t], w[t], yA ? yA[t] : nullptr, yD[t], grad_w[t], &out[t], cur,
+                                 status_dev ? status_dev + t : nullptr);
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = cudaMemcpyAsync(base, &I, sizeof(I), cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(base, table.data(), (size_t)count * sizeof(ff::AdjInst),
+                                    cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return FF_ERR_CUDA;
-    ff::adjoint_single_kernel<<<1, ff::kAdjThreads, 0, st>>>((const ff::AdjInst*)base);
+    ff::adjoint_single_kernel<<<count, ff::kAdjThreads, 0, st>>>((const ff::AdjInst*)base);
     e = cudaGetLastError();
     if (e != cudaSuccess) return FF_ERR_CUDA;
-    if (status_dev) {
-        e = cudaMemcpyAsync(status_dev, I.flags + 1, sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
-        if (e != cudaSuccess) return FF_ERR_CUDA;
-    }
     return FF_OK;
+}
+
+int ff_backward_single(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,
+                       const ff_grads* out, void* ws, size_t ws_bytes, int32_t* status_dev, void* stream) {
+    if (!ff::valid_backward(p, w, yA, yD, grad_w, out)) return FF_ERR_INVALID_ARG;
+    const void* wv[1] = {w};
+    const void* ya[1] = {yA};
+    const void* yd[1] = {yD};
+    const void* gv[1] = {grad_w};
+    return ff_backward_batch(p, 1, wv, ya, yd, gv, out, ws, ws_bytes, status_dev, stream);
 }
 
 }  // extern "C"

@@ -678,8 +678,9 @@ int ff_solve_multi(const ff_problem* p, const ff_options* o, void* ws, size_t ws
 }
 
 int ff_solve_batch(const ff_problem* probs, int count, const ff_options* o, void* ws, size_t ws_bytes,
-                   ff_result* result_dev, void* const* w_out, void* stream) {
-    return ff::dispatch(probs, count, o, ws, ws_bytes, result_dev, w_out, nullptr, nullptr, stream);
+                   ff_result* result_dev, void* const* w_out, void* const* yA_out, void* const* yD_out,
+                   void* stream) {
+    return ff::dispatch(probs, count, o, ws, ws_bytes, result_dev, w_out, yA_out, yD_out, stream);
 }
 
 int ff_batch_plan(const ff_problem* probs, int count, const ff_options* o_in, int32_t* cluster_out,

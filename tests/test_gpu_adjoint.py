@@ -119,3 +119,32 @@ def test_autograd_return_minus_risk(torch_mod):
         b = float(np.sum(explicit[nm] * delta)) + OG.directional_vjp(prob, sol, g, nm, delta)
         scale = float(np.linalg.norm(grad) * np.linalg.norm(delta))
         assert abs(a - b) <= TOL_GRAD * abs(b) + 1e-7 * scale, (nm, a, b)
+
+
+def test_batched_backward_matches_oracle(torch_mod):
+    """ff_backward_batch over several instances in one launch (through
+    BatchRunner with duals) gives each instance's oracle derivative."""
+    torch = torch_mod
+    from paper_2604_22625_gb300 import api
+    probs = [CASES["dead_rows_f64"][0](), CASES["budget_zeros_f64"][0](), S.make_single(300, 12, 44, n_onehot=4)]
+    br = api.BatchRunner(probs, precision="f64", duals=True, tol=1e-10)
+    br.prepare_backward()
+    rng = np.random.default_rng(21)
+    gs = [rng.standard_normal(p.n) for p in probs]
+    for i, g in enumerate(gs):
+        o = int(br.w_off[i])
+        br.g_dev[o:o + probs[i].n] = torch.tensor(g, dtype=br.g_dev.dtype, device=br.g_dev.device)
+    br.run()
+    br.backward()
+    torch.cuda.synchronize()
+    assert all(i["status_name"] == "converged" for i in br.results())
+    assert int(br.bstatus.abs().sum().item()) == 0
+    for i, p in enumerate(probs):
+        sol = oracle.solve(p)
+        for nm in OG.PARAMS:
+            grad = br.gradient(i, nm)
+            delta = rng.standard_normal(grad.shape)
+            a = float(np.sum(grad * delta))
+            b = OG.directional_vjp(p, sol, gs[i], nm, delta)
+            scale = float(np.linalg.norm(grad) * np.linalg.norm(delta))
+            assert abs(a - b) <= TOL_GRAD * abs(b) + 1e-7 * scale, (i, nm, a, b)
