@@ -55,17 +55,20 @@ inline Sizes sizes_of(const ff_problem& p, int precision) {
     s.R = s.multi ? p.T : 1;
     s.np = (p.n + 31) / 32 * 32;
     s.omega_diag = p.omega_diag ? 1 : 0;
+    int vcap = 0;
     const int CH = (s.P <= 64 && s.k + s.m <= 2 * kThreads)
-                       ? choose_tile(s.P, s.k, s.m, s.omega_diag, matvec_elem(precision), panel_elem(precision))
+                       ? choose_tile(s.P, s.n, s.k, s.m, s.omega_diag, matvec_elem(precision),
+                                     panel_elem(precision), &vcap)
                        : 0;
     s.tl = make_tiling(s.n, s.k, s.m, CH > 0 ? CH : 8);
     s.tl.CH = CH;
+    s.tl.vcap = vcap;
     return s;
 }
 
 inline size_t smem_of(const Sizes& s, int precision) {
     return solver_smem_bytes(s.P, s.k, s.m, s.omega_diag, matvec_elem(precision), s.tl.CH, s.tl.Rp,
-                             panel_elem(precision));
+                             panel_elem(precision), s.tl.vcap);
 }
 
 inline size_t panel_bytes(const Sizes& s, int precision) {
@@ -222,14 +225,14 @@ __device__ void repack_one(const ff_problem& p, const Inst<M, S>& I, double lam2
         for (int pp = 0; pp < P; ++pp) {
             double dv = in ? (double)D[(size_t)pp * n + i] : 0.0;
             double av = in ? (double)al[(size_t)pp * n + i] : 0.0;
-            ((double*)I.Dp)[(size_t)pp * np + i] = (double)dv;
-            ((double*)I.alpha)[(size_t)pp * np + i] = (double)av;
+            ((M*)I.Dp)[(size_t)pp * np + i] = (M)dv;
+            ((M*)I.alpha)[(size_t)pp * np + i] = (M)av;
             dmax = fmax(dmax, dv);
         }
         ((double*)I.Dmax)[i] = (double)dmax;
         for (int r = 0; r < R; ++r) {
-            ((double*)I.c1)[(size_t)r * np + i] = (double)(in ? lam2 * (double)s[(size_t)r * n + i] : 0.0);
-            ((double*)I.c2)[(size_t)r * np + i] = (double)(in ? lam3 * (double)q[(size_t)r * n + i] : 0.0);
+            ((M*)I.c1)[(size_t)r * np + i] = (M)(in ? lam2 * (double)s[(size_t)r * n + i] : 0.0);
+            ((M*)I.c2)[(size_t)r * np + i] = (M)(in ? lam3 * (double)q[(size_t)r * n + i] : 0.0);
         }
         ((double*)I.w0)[i] = (double)(in ? (double)w0[i] : 0.0);
         ((double*)I.cen)[i] = (double)((in && I.multi) ? (double)wT[i] : 0.0);
@@ -260,19 +263,19 @@ Inst<M, S> carve(const ff_problem& p, const Sizes& s, unsigned char*& cur, void*
     I.omega_diag = p.omega_diag ? 1 : 0;
     auto take = [&](size_t bytes) { unsigned char* r = cur; cur += a256(bytes); return (void*)r; };
     const size_t r = sizeof(double);
-    I.CH = s.tl.CH; I.kp = s.tl.kp; I.mp = s.tl.mp; I.Rp = s.tl.Rp; I.ntile = s.tl.ntile;
+    I.CH = s.tl.CH; I.kp = s.tl.kp; I.mp = s.tl.mp; I.Rp = s.tl.Rp; I.ntile = s.tl.ntile; I.vcap = s.tl.vcap;
     const size_t pb = (size_t)s.tl.ntile * s.tl.Rp * s.tl.CH * sizeof(S);
     I.PE = (const S*)take(pb);
     I.PR = (const S*)take(pb);
     I.Om = (const double*)take((size_t)(I.omega_diag ? s.k : s.k * s.k) * r);
-    I.alpha = (const double*)take((size_t)s.P * s.np * r);
-    I.Dp = (const double*)take((size_t)s.P * s.np * r);
+    I.alpha = (const M*)take((size_t)s.P * s.np * r);
+    I.Dp = (const M*)take((size_t)s.P * s.np * r);
     I.Dmax = (const double*)take((size_t)s.np * r);
     I.w0 = (const double*)take((size_t)s.np * r);
     I.cen = (const double*)take((size_t)s.np * r);
     I.alphaT = (const double*)take((size_t)s.np * r);
-    I.c1 = (const double*)take((size_t)s.R * s.np * r);
-    I.c2 = (const double*)take((size_t)s.R * s.np * r);
+    I.c1 = (const M*)take((size_t)s.R * s.np * r);
+    I.c2 = (const M*)take((size_t)s.R * s.np * r);
     I.L = (const double*)take((size_t)s.m * r + 16);
     I.U = (const double*)take((size_t)s.m * r + 16);
     I.x = (double*)take((size_t)s.P * s.np * r);

@@ -30,6 +30,7 @@ constexpr int kSmemLimit = 227 * 1024 - 2048;   // dynamic shared memory per CTA
 // that one bulk copy moves into shared memory.
 struct Tiling {
     int CH, kp, mp, Rp, ntile;
+    int vcap;             // single period: entries of v kept in shared memory (0: v in the workspace)
 };
 
 __host__ __device__ inline Tiling make_tiling(int n, int k, int m, int CH) {
@@ -39,6 +40,7 @@ __host__ __device__ inline Tiling make_tiling(int n, int k, int m, int CH) {
     t.mp = (m + 7) / 8 * 8;
     t.Rp = t.kp + t.mp;
     t.ntile = (n + CH - 1) / CH;
+    t.vcap = 0;
     return t;
 }
 
@@ -50,14 +52,15 @@ template <class M, class S>
 struct Inst {
     int n, k, m, P, R, multi, np, omega_diag;
     int CH, kp, mp, Rp, ntile; // panel tiling (see Tiling)
+    int vcap;                  // > 0: v lives in shared memory (single period)
     const S* PE;          // ntile tiles of [Rp][CH]
     const S* PR;          // ntile tiles of [CH][Rp]
     const double* Om;     // k x k, or k diagonal entries
-    const double* alpha;  // P x np
-    const double* Dp;     // P x np
+    const M* alpha;       // P x np   (matvec precision: FP32 inputs stay exact)
+    const M* Dp;          // P x np
     const double* Dmax;   // np       max over periods of D (for the Lipschitz bound)
-    const double* c1;     // R x np   lambda2 * s
-    const double* c2;     // R x np   lambda3 * q
+    const M* c1;          // R x np   lambda2 * s
+    const M* c2;          // R x np   lambda3 * q
     const double* w0;     // np
     const double* cen;    // np       risk centre: w_T (multi) or 0 (single)
     const double* alphaT; // np       alpha at t = T (multi) or unused
@@ -93,11 +96,13 @@ struct Params {
 };
 
 // Shared-memory bytes the solver kernel needs for these sizes and tiling.
-size_t solver_smem_bytes(int P, int k, int m, int omega_diag, size_t matvec_size, int CH, int Rp, size_t panel_size);
+size_t solver_smem_bytes(int P, int k, int m, int omega_diag, size_t matvec_size, int CH, int Rp, size_t panel_size,
+                         int vcap);
 
-// Largest tile width CH (256 down to 8) whose shared-memory layout fits;
-// 0 if none does.
-int choose_tile(int P, int k, int m, int omega_diag, size_t matvec_size, size_t panel_size);
+// Largest tile width CH (256 down to 8) whose shared-memory layout fits, 0 if
+// none does; for a single period it first tries to keep v (n entries, FP64)
+// in shared memory as well and reports the capacity in *vcap (else 0).
+int choose_tile(int P, int n, int k, int m, int omega_diag, size_t matvec_size, size_t panel_size, int* vcap);
 
 // Launch the team kernel over `count` instances (insts is a device array).
 // G = CTAs per instance (cluster size), nteams = concurrent teams; single =

@@ -56,8 +56,10 @@ struct Layout {
     size_t cand, thprev, theta, thq;
     size_t lb, ubd;            // double, m each
     size_t bars;               // kStages mbarriers
+    size_t vbuf;               // double, vcap (single period, v in shared memory)
     size_t ring;               // kStages panel tiles
-    size_t tile_bytes;
+    size_t panel_bytes;        // panel tile bytes within a stage (128-aligned)
+    size_t tile_bytes;         // stage stride
     size_t total;
     int vlen, slen;
 };
@@ -65,7 +67,7 @@ struct Layout {
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 __host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_diag, size_t ms, int CH, int Rp,
-                                              size_t ps) {
+                                              size_t ps, int vcap) {
     Layout L;
     const int pct0 = P < kPC ? P : kPC;
     const int pct = pct0 <= 1 ? 1 : (pct0 <= 2 ? 2 : (pct0 <= 4 ? 4 : 8));   // template chunk width
@@ -102,8 +104,12 @@ __host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_dia
     L.thq = take((size_t)P * 8);
     L.lb = take((size_t)m * 8);
     L.ubd = take((size_t)m * 8);
+    L.vbuf = take((size_t)vcap * 8);
     o = align_up(o, 128);
-    L.tile_bytes = align_up((size_t)Rp * CH * ps, 128);
+    // one stage: the panel tile, then (single period) the per-asset vectors that
+    // the fused passes stage with it: 5 FP64 (x, x0, yD, yD0, w0) + 2 M (c1, c2)
+    L.panel_bytes = align_up((size_t)Rp * CH * ps, 128);
+    L.tile_bytes = L.panel_bytes + (P == 1 ? align_up((size_t)CH * (5 * 8 + 2 * ms), 128) : 0);
     L.ring = o;
     o += (size_t)kStages * L.tile_bytes;
     L.total = o;
@@ -111,19 +117,26 @@ __host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_dia
 }
 
 size_t solver_smem_bytes(int P, int k, int m, int omega_diag, size_t matvec_size, int CH, int Rp,
-                         size_t panel_size) {
-    return make_layout(P, k, m, omega_diag, matvec_size, CH, Rp, panel_size).total;
+                         size_t panel_size, int vcap) {
+    return make_layout(P, k, m, omega_diag, matvec_size, CH, Rp, panel_size, vcap).total;
 }
 
-int choose_tile(int P, int k, int m, int omega_diag, size_t matvec_size, size_t panel_size) {
+int choose_tile(int P, int n, int k, int m, int omega_diag, size_t matvec_size, size_t panel_size, int* vcap) {
     const int Rp = (k + 7) / 8 * 8 + (m + 7) / 8 * 8;
     // the single-period variant is built for kSingleCtasPerSm resident CTAs
     const size_t limit = P == 1 ? (size_t)kSmemLimit / kSingleCtasPerSm - 1024 : (size_t)kSmemLimit;
     const size_t max_tile = P == 1 ? (size_t)kMaxTileBytes / kSingleCtasPerSm : (size_t)kMaxTileBytes;
-    for (int CH = 256; CH >= 8; CH /= 2) {
-        if ((size_t)Rp * CH * panel_size > max_tile) continue;
-        if (make_layout(P, k, m, omega_diag, matvec_size, CH, Rp, panel_size).total <= limit) return CH;
+    for (int pass = (P == 1 ? 0 : 1); pass < 2; ++pass) {
+        for (int CH = 256; CH >= 8; CH /= 2) {
+            if ((size_t)Rp * CH * panel_size > max_tile) continue;
+            const int vc = pass == 0 ? (n + CH - 1) / CH * CH : 0;
+            if (make_layout(P, k, m, omega_diag, matvec_size, CH, Rp, panel_size, vc).total <= limit) {
+                *vcap = vc;
+                return CH;
+            }
+        }
     }
+    *vcap = 0;
     return 0;
 }
 
@@ -168,6 +181,26 @@ __device__ __forceinline__ void pipe_issue(Pipe& pp, const void* src, unsigned b
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                      ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
                      : "memory");
+    }
+    pp.tail = pp.tail + 1 == kStages ? 0 : pp.tail + 1;
+    ++pp.inflight;
+}
+
+// Issue up to 8 copies into the tail stage that complete on its one barrier:
+// copy q moves bytes[q] from src[q] to the stage offset off[q].
+__device__ __forceinline__ void pipe_issue_n(Pipe& pp, int nc, const void* const* src, const unsigned* off,
+                                             const unsigned* bytes) {
+    if (threadIdx.x == 0) {
+        unsigned total = 0;
+        for (int q = 0; q < nc; ++q) total += bytes[q];
+        const unsigned bar = smem_u32(&pp.bars[pp.tail]);
+        unsigned char* stage = pp.ring + (size_t)pp.tail * pp.stride;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(total) : "memory");
+        for (int q = 0; q < nc; ++q) {
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(smem_u32(stage + off[q])), "l"(src[q]), "r"(bytes[q]), "r"(bar)
+                         : "memory");
+        }
     }
     pp.tail = pp.tail + 1 == kStages ? 0 : pp.tail + 1;
     ++pp.inflight;
@@ -308,6 +341,7 @@ struct Ctx {
     int n, k, m, P, R, np;
     int i0, i1;
     int t0, t1;                // panel tiles of this CTA
+    unsigned panel_off;        // offset of the per-asset vectors within a stage
     int G, g;
     Pipe pipe;
     int tid, lane, warp;
@@ -422,12 +456,14 @@ template <class M> struct RowLoad<M, double> {
 // first lane (one owner per entry: no races, fixed order).  Null vectors give
 // zeros.
 // ---------------------------------------------------------------------------
+// Products of one PR tile with the staged vectors, added into vpart (FP64).
+// sv0A/sv1A feed the A rows, sv0F/sv1F the F rows ([PCT][CH] each).
 template <int PCT, class AT, class M, class S>
-__device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, const double* a1,
-                               const double* f0, const double* f1, bool subcen) {
+__device__ __forceinline__ void reduce_tile(Ctx<M, S>& c, const S* tile, const AT* sv0A, const AT* sv1A,
+                                            const AT* sv0F, const AT* sv1F, int cnt, int pc, bool has1) {
     constexpr int RPT = 4;
     const int CH = c.I.CH, Rp = c.I.Rp, kp = c.I.kp;
-    const int m = c.m, k = c.k, np = c.np, n = c.n;
+    const int m = c.m, k = c.k;
     const int Lr = 2 * m + 2 * k;
     const int ngr = Rp / RPT;
     int na = 1;
@@ -436,7 +472,67 @@ __device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, c
     const bool active = grp < ngr;
     const int r0 = grp * RPT;
     const bool isA = r0 >= kp;
+    AT acc[RPT][2][PCT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int q = 0; q < PCT; ++q) { acc[r][0][q] = 0; acc[r][1][q] = 0; }
+    if (active) {
+        const AT* sv0 = isA ? sv0A : sv0F;
+        const AT* sv1 = isA ? sv1A : sv1F;
+        for (int ii = lane_a; ii < cnt; ii += na) {
+            AT w[RPT];
+            RowLoad<AT, S>::load(tile + (size_t)ii * Rp + r0, w);
+#pragma unroll
+            for (int q = 0; q < PCT; ++q) {
+                const AT x0 = sv0[q * CH + ii];
+                const AT x1 = has1 ? sv1[q * CH + ii] : (AT)0;
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    acc[r][0][q] += w[r] * x0;
+                    acc[r][1][q] += w[r] * x1;
+                }
+            }
+        }
+    }
+    for (int off = na / 2; off > 0; off >>= 1) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+            for (int q = 0; q < PCT; ++q) {
+                acc[r][0][q] += __shfl_xor_sync(0xffffffffu, acc[r][0][q], off);
+                acc[r][1][q] += __shfl_xor_sync(0xffffffffu, acc[r][1][q], off);
+            }
+    }
+    if (active && lane_a == 0) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int row = r0 + r;
+            int o0 = -1, o1 = -1;
+            if (!isA && row < k) { o0 = 2 * m + row; o1 = 2 * m + k + row; }
+            if (isA && row - kp < m) { o0 = row - kp; o1 = m + row - kp; }
+            if (o0 >= 0) {
+#pragma unroll
+                for (int q = 0; q < PCT; ++q) {
+                    if (q < pc) {
+                        c.vpart[q * Lr + o0] += (double)acc[r][0][q];
+                        c.vpart[q * Lr + o1] += (double)acc[r][1][q];
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int PCT, class AT, class M, class S>
+__device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, const double* a1,
+                               const double* f0, const double* f1, bool subcen) {
+    const int CH = c.I.CH, Rp = c.I.Rp;
+    const int m = c.m, k = c.k, np = c.np, n = c.n;
+    const int Lr = 2 * m + 2 * k;
     const bool has1 = (a1 != nullptr) || (f1 != nullptr);
+    // the F-row vectors are the A-row vectors (no centre, same arrays): stage two
+    const bool single_fa = !c.I.multi && a0 != nullptr && a1 != nullptr && f0 == a1 && (f1 == nullptr || f1 == a0);
     const size_t tile_elems = (size_t)Rp * CH;
     const unsigned bytes = (unsigned)(tile_elems * sizeof(S));
     AT* st = (AT*)c.stage;  // [4][PCT][CH]
@@ -447,7 +543,10 @@ __device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, c
         const int t = c.t0 + j;
         const int ib = t * CH;
         const int cnt = min(CH, n - ib);
-        for (int e = c.tid; e < 4 * PCT * CH; e += kThreads) {
+        // single period (centre 0): the F rows take the same two vectors as the
+        // A rows, in swapped roles (f0 = a1, f1 = a0), so only two are staged
+        const int nvec = single_fa ? 2 : 4;
+        for (int e = c.tid; e < nvec * PCT * CH; e += kThreads) {
             const int vec = e / (PCT * CH);
             const int q = (e / CH) % PCT;
             const int ii = e % CH;
@@ -461,60 +560,100 @@ __device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, c
         }
         const S* tile = (const S*)pipe_wait(c.pipe);
         __syncthreads();
-        AT acc[RPT][2][PCT];
-#pragma unroll
-        for (int r = 0; r < RPT; ++r)
-#pragma unroll
-            for (int q = 0; q < PCT; ++q) { acc[r][0][q] = 0; acc[r][1][q] = 0; }
-        if (active) {
-            const AT* sv0 = st + (isA ? 0 : 2) * PCT * CH;
-            const AT* sv1 = st + (isA ? 1 : 3) * PCT * CH;
-            for (int ii = lane_a; ii < cnt; ii += na) {
-                AT w[RPT];
-                RowLoad<AT, S>::load(tile + (size_t)ii * Rp + r0, w);
-#pragma unroll
-                for (int q = 0; q < PCT; ++q) {
-                    const AT x0 = sv0[q * CH + ii];
-                    const AT x1 = has1 ? sv1[q * CH + ii] : (AT)0;
-#pragma unroll
-                    for (int r = 0; r < RPT; ++r) {
-                        acc[r][0][q] += w[r] * x0;
-                        acc[r][1][q] += w[r] * x1;
-                    }
-                }
-            }
-        }
-        for (int off = na / 2; off > 0; off >>= 1) {
-#pragma unroll
-            for (int r = 0; r < RPT; ++r)
-#pragma unroll
-                for (int q = 0; q < PCT; ++q) {
-                    acc[r][0][q] += __shfl_xor_sync(0xffffffffu, acc[r][0][q], off);
-                    acc[r][1][q] += __shfl_xor_sync(0xffffffffu, acc[r][1][q], off);
-                }
-        }
-        if (active && lane_a == 0) {
-#pragma unroll
-            for (int r = 0; r < RPT; ++r) {
-                const int row = r0 + r;
-                int o0 = -1, o1 = -1;
-                if (!isA && row < k) { o0 = 2 * m + row; o1 = 2 * m + k + row; }
-                if (isA && row - kp < m) { o0 = row - kp; o1 = m + row - kp; }
-                if (o0 >= 0) {
-#pragma unroll
-                    for (int q = 0; q < PCT; ++q) {
-                        if (q < pc) {
-                            c.vpart[q * Lr + o0] += (double)acc[r][0][q];
-                            c.vpart[q * Lr + o1] += (double)acc[r][1][q];
-                        }
-                    }
-                }
-            }
-        }
+        reduce_tile<PCT, AT>(c, tile, st, st + PCT * CH, st + (single_fa ? 1 : 2) * PCT * CH,
+                             st + (single_fa ? 0 : 3) * PCT * CH, cnt, pc, has1);
         __syncthreads();
         pipe_pop(c.pipe);
         if (j + kStages < nt) pipe_issue(c.pipe, c.I.PR + (size_t)(t + kStages) * tile_elems, bytes);
     }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Single-period fused pass (elementwise prox + Halpern + reduce): each PR tile
+// arrives together with its assets' x, x0, y_D, y_D0, w0 (FP64) and c1, c2
+// (M) in one stage.  For the tile's assets the threads form
+//   x_bar = Proj(v) (threshold theta),  x+ = hlA x_bar + hlB x + hlC x0,
+//   y_bar = sigma-prox of the trade cost at y + sigma (2 x_bar - x),  y+ likewise,
+// write x+ and y+ (and, at checks, x_bar and y_bar) to the workspace, stage
+// x_bar and x+ as M, and the panel products of the tile follow:
+//   A x_bar, A x+ (A rows);  F^T x+, F^T x_bar (F rows; no centre).
+// ---------------------------------------------------------------------------
+template <class M, class S>
+__device__ void reduce_fused_single(Ctx<M, S>& c, double hlA, double hlB, double hlC, double sD, double inv_sD,
+                                    double dexp, bool check, double (&rloc)[2]) {
+    const int CH = c.I.CH, Rp = c.I.Rp;
+    const int m = c.m, k = c.k, n = c.n, np = c.np;
+    const int Lr = 2 * m + 2 * k;
+    const size_t tile_elems = (size_t)Rp * CH;
+    const unsigned pbytes = (unsigned)(tile_elems * sizeof(S));
+    const unsigned po = c.panel_off;
+    const unsigned off[8] = {0u, po, po + 8u * CH, po + 16u * CH, po + 24u * CH, po + 32u * CH, po + 40u * CH,
+                             po + 40u * CH + (unsigned)sizeof(M) * CH};
+    M* st = c.stage;  // [2][CH]: x_bar, x+
+    const double theta = c.theta[0];
+    for (int e = c.tid; e < Lr; e += kThreads) c.vpart[e] = 0;
+    auto issue = [&](int t) {
+        const int ib = t * CH;
+        const unsigned nv = (unsigned)min(CH, np - ib);
+        const void* src[8] = {c.I.PR + (size_t)t * tile_elems, c.I.x + ib, c.I.x0 + ib, c.I.yD + ib, c.I.yD0 + ib,
+                              c.I.w0 + ib, c.I.c1 + ib, c.I.c2 + ib};
+        const unsigned bytes[8] = {pbytes, 8u * nv, 8u * nv, 8u * nv, 8u * nv, 8u * nv, (unsigned)sizeof(M) * nv,
+                                   (unsigned)sizeof(M) * nv};
+        pipe_issue_n(c.pipe, 8, src, off, bytes);
+    };
+    const int nt = c.t1 - c.t0;
+    for (int j = 0; j < nt && j < kStages; ++j) issue(c.t0 + j);
+    for (int j = 0; j < nt; ++j) {
+        const int t = c.t0 + j;
+        const int ib = t * CH;
+        const int cnt = min(CH, n - ib);
+        const unsigned char* stg = pipe_wait(c.pipe);
+        const S* tile = (const S*)stg;
+        const double* sx = (const double*)(stg + off[1]);
+        const double* sx0 = (const double*)(stg + off[2]);
+        const double* syd = (const double*)(stg + off[3]);
+        const double* syd0 = (const double*)(stg + off[4]);
+        const double* sw0 = (const double*)(stg + off[5]);
+        const M* sc1 = (const M*)(stg + off[6]);
+        const M* sc2 = (const M*)(stg + off[7]);
+        for (int ii = c.tid; ii < cnt; ii += kThreads) {
+            const int i = ib + ii;
+            const double vv = c.I.v[i];
+            const double av = fabs(vv) - theta;
+            const double xb = av > 0 ? (vv < 0 ? -av : av) : 0.0;
+            const double xc = sx[ii];
+            const double xn = hlA * xb + hlB * xc + hlC * sx0[ii];
+            const double dxe = 2.0 * xb - xc;          // (Delta (2 x_bar - x))_1
+            const double b = -sw0[ii];
+            const double yd = syd[ii];
+            const double pD = yd + sD * dxe;
+            const double tt = pD * inv_sD + b;
+            M ylive;
+            const double ydb = trade_multiplier<M>(tt, inv_sD, (double)sc1[ii], (double)sc2[ii], dexp, ylive)
+                                   ? (double)ylive
+                                   : pD + sD * b;
+            const double ydn = hlA * ydb + hlB * yd + hlC * syd0[ii];
+            c.I.xn[i] = xn;
+            c.I.yDn[i] = ydn;
+            if (check) {
+                c.I.xb[i] = xb;
+                c.I.yDb[i] = ydb;
+                rloc[0] += (xc - xb) * (xc - xb);
+                rloc[1] += (yd - ydb) * (yd - ydb);
+            }
+            st[ii] = (M)xb;
+            st[CH + ii] = (M)xn;
+        }
+        __syncthreads();
+        // A rows: (x_bar, x+); F rows: (x+, x_bar)
+        reduce_tile<1, M>(c, tile, st, st + CH, st + CH, st, cnt, 1, true);
+        __syncthreads();
+        pipe_pop(c.pipe);
+        if (j + kStages < nt) issue(t + kStages);
+    }
+    // the x+ / y+ written here are read by bulk copies (async proxy) next iteration
+    asm volatile("fence.proxy.async.global;" ::: "memory");
     __syncthreads();
 }
 
@@ -646,6 +785,52 @@ __device__ void expand_pass(Ctx<M, S>& c, int Pv, const W* wF, const W* wA, Epi 
         __syncthreads();
         pipe_pop(c.pipe);
         if (j + kStages < nt) pipe_issue(c.pipe, c.I.PE + (size_t)(t + kStages) * tile_elems, bytes);
+    }
+}
+
+// Single-period main expand pass: the PE tile arrives with its assets' x, y_D
+// (FP64) and alpha, D (M) in one stage; v = x - tau (grad f(x) + K^T y).
+template <class M, class S>
+__device__ void expand_main_single(Ctx<M, S>& c, double tau, double kap, const M* wF, const M* wA) {
+    const int CH = c.I.CH, Rp = c.I.Rp;
+    const int n = c.n, np = c.np;
+    const size_t tile_elems = (size_t)Rp * CH;
+    const unsigned pbytes = (unsigned)(tile_elems * sizeof(S));
+    const unsigned po = c.panel_off;
+    const unsigned off[5] = {0u, po, po + 8u * CH, po + 16u * CH, po + 16u * CH + (unsigned)sizeof(M) * CH};
+    const M kapm = (M)kap;
+    double* v = c.I.v;
+    auto issue = [&](int t) {
+        const int ib = t * CH;
+        const unsigned nv = (unsigned)min(CH, np - ib);
+        const void* src[5] = {c.I.PE + (size_t)t * tile_elems, c.I.x + ib, c.I.yD + ib, c.I.alpha + ib,
+                              c.I.Dp + ib};
+        const unsigned bytes[5] = {pbytes, 8u * nv, 8u * nv, (unsigned)sizeof(M) * nv, (unsigned)sizeof(M) * nv};
+        pipe_issue_n(c.pipe, 5, src, off, bytes);
+    };
+    const int nt = c.t1 - c.t0;
+    for (int j = 0; j < nt && j < kStages; ++j) issue(c.t0 + j);
+    for (int j = 0; j < nt; ++j) {
+        const int t = c.t0 + j;
+        const int ib = t * CH;
+        const int cnt = min(CH, n - ib);
+        const unsigned char* stg = pipe_wait(c.pipe);
+        const S* tile = (const S*)stg;
+        const double* sx = (const double*)(stg + off[1]);
+        const double* syd = (const double*)(stg + off[2]);
+        const M* sal = (const M*)(stg + off[3]);
+        const M* sdp = (const M*)(stg + off[4]);
+        auto epi = [&](int i, int p, double aF, double aA) {
+            const int ii = i - ib;
+            const double xv = sx[ii];
+            const M gf = -sal[ii] + (M)2 * kapm * ((M)aF + sdp[ii] * (M)xv);
+            const M kt = (M)aA + (M)syd[ii];
+            v[i] = xv - tau * (double)(gf + kt);
+        };
+        expand_tile<1, M>(c, tile, ib, cnt, 0, 1, wF, wA, epi);
+        __syncthreads();
+        pipe_pop(c.pipe);
+        if (j + kStages < nt) issue(t + kStages);
     }
 }
 
@@ -831,10 +1016,14 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         c.i1 = min(c.n, c.t1 * c.I.CH);
         const int n = c.n, k = c.k, m = c.m, P = c.P, R = c.R, np = c.np;
         const int Lr = 2 * m + 2 * k;
-        const Layout Ly = make_layout(P, k, m, c.I.omega_diag, sizeof(M), c.I.CH, c.I.Rp, sizeof(S));
+        const Layout Ly = make_layout(P, k, m, c.I.omega_diag, sizeof(M), c.I.CH, c.I.Rp, sizeof(S), c.I.vcap);
+        // v in shared memory holds this CTA's assets [i0, i1): offset the
+        // pointer so that v[i] addresses entry i - i0
+        if (PCMAX == 1 && c.I.vcap > 0) c.I.v = (double*)(smem + Ly.vbuf) - c.i0;
         pipe.ring = smem + Ly.ring;
         pipe.stride = Ly.tile_bytes;
         c.pipe = pipe;
+        c.panel_off = (unsigned)Ly.panel_bytes;
         if (threadIdx.x == 0) pipe_err_s = 0;
         c.vpart = (double*)(smem + Ly.vpart);
         c.vout = (double*)(smem + Ly.vout);
@@ -951,6 +1140,8 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             c.thprev[p] = 0;
             c.thq[p] = 0;
         }
+        // the initial iterate is read by bulk copies (async proxy)
+        asm volatile("fence.proxy.async.global;" ::: "memory");
         __syncthreads();
         // u = F^T (x - c), ax = A x
         for (int p0 = 0; p0 < P; p0 += kPC) {
@@ -983,10 +1174,14 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             const bool check = (it % prm.check_every) == 0;
             const double cj = (double)(j + 1) / (double)(j + 2);
             const double oj = 1.0 - cj;
+            // Halpern step z+ = hlA T(z) + hlB z + hlC z_anchor
+            const double hlA = cj * (1.0 + rho), hlB = -cj * rho, hlC = oj;
             // (1) om = Omega u
             apply_omega_m(c, c.u, c.om, P);
             // (2) expand: v = x - tau (grad f(x) + K^T y)
-            {
+            if constexpr (PCMAX == 1) {
+                expand_main_single(c, tau, kap, c.om, c.yAm);
+            } else {
                 const double* x = c.I.x;
                 const double* yD = c.I.yD;
                 double* v = c.I.v;
@@ -1006,8 +1201,9 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             th_rounds += l1_thresholds(cl, c, c.I.v, c.theta, c.thprev);
             lap(2);
             // (4) elementwise: x_bar, y_D bar, Halpern combination, residual parts
+            //     (fused into the reduce pass for a single period)
             double rloc[2] = {0, 0};
-            {
+            if constexpr (PCMAX != 1) {
                 const double* x = c.I.x;
                 const double* v = c.I.v;
                 for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
@@ -1024,7 +1220,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                             const double xc = x[o];
                             c.I.xb[o] = xb;
                             xe = 2.0 * xb - xc;
-                            c.I.xn[o] = cj * ((1.0 + rho) * xb - rho * xc) + oj * c.I.x0[o];
+                            c.I.xn[o] = hlA * xb + hlB * xc + hlC * c.I.x0[o];
                             if (check) rloc[0] += (xc - xb) * (xc - xb);
                         }
                         const double dxe = xe - xe_prev;   // (Delta xe)_r; last multi row: -xe_{P-1}
@@ -1039,7 +1235,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                                                ? (double)ylive
                                                : pD + sD * b;
                         c.I.yDb[orr] = ydb;
-                        c.I.yDn[orr] = cj * ((1.0 + rho) * ydb - rho * yd) + oj * c.I.yD0[orr];
+                        c.I.yDn[orr] = hlA * ydb + hlB * yd + hlC * c.I.yD0[orr];
                         if (check) rloc[1] += (yd - ydb) * (yd - ydb);
                     }
                 }
@@ -1051,7 +1247,10 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             double rA = 0, pin = 0, nAx = 0, nCl = 0;
             for (int p0 = 0; p0 < P; p0 += kPC) {
                 const int pc = min(kPC, P - p0);
-                reduce_chunk<PCMAX>(c, p0, pc, c.I.xb, c.I.xn, c.I.xn, (const double*)nullptr, true);
+                if constexpr (PCMAX == 1)
+                    reduce_fused_single(c, hlA, hlB, hlC, sD, inv_sD, dexp, check, rloc);
+                else
+                    reduce_chunk<PCMAX>(c, p0, pc, c.I.xb, c.I.xn, c.I.xn, (const double*)nullptr, true);
                 team_reduce<false>(cl, c.vpart, c.vout, pc * Lr, G, g);
                 for (int e = c.tid; e < pc * m; e += kThreads) {
                     const int q = e / m, jj = e % m;
@@ -1063,7 +1262,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                     const double qq = pA / sA;
                     const double cl_ = qq > c.ubd[jj] ? c.ubd[jj] : (qq < c.lb[jj] ? c.lb[jj] : qq);
                     const double yab = pA - sA * cl_;
-                    const double yan = cj * ((1.0 + rho) * yab - rho * ya) + oj * c.I.yA0[pe];
+                    const double yan = hlA * yab + hlB * ya + hlC * c.I.yA0[pe];
                     c.yAb[pe] = yab;
                     c.yA[pe] = yan;
                     c.yAm[pe] = (M)yan;
@@ -1263,6 +1462,8 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                     for (int r = 0; r < R; ++r) c.I.yD0[(size_t)r * np + i] = c.I.yD[(size_t)r * np + i];
                 }
                 for (int e = c.tid; e < P * m; e += kThreads) c.I.yA0[e] = c.yA[e];
+                // the new anchor is read by bulk copies (async proxy) from here on
+                asm volatile("fence.proxy.async.global;" ::: "memory");
                 __syncthreads();
                 j = 0;
                 ++restarts;
