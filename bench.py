@@ -36,6 +36,8 @@ if ROOT not in sys.path:
 
 import numpy as np  # noqa: E402
 
+from paper_2604_22625_gb300.replicas import dist_env, max_over_ranks, rank_seed, sum_over_ranks  # noqa: E402
+
 METRIC = "solves/sec at 1e-6 rel. KKT on 1 GB300 (batched vs plain form); % HBM roofline"
 UNIT = "solves/s"
 TOL = 1e-6
@@ -66,23 +68,23 @@ def make_workload(name: str, rank: int):
     """(problems, precision, description) of a named workload; rank seeds it."""
     from paper_2604_22625_gb300 import synthetic as S
     if name == "batch":
-        probs = S.config_batch(seed=3 + 10 * rank)
+        probs = S.config_batch(seed=rank_seed(3, rank))
         desc = ("batched mixed precision: 512 single-period (n~U{500..8000}, k in {40,80}) + "
                 "64 multi-period (T~U{5..40}, n~U{1000..4000}) instances")
         return probs, "bf16", desc
     if name == "batch_profile":
-        probs = [p for p in S.config_batch(seed=3 + 10 * rank, n_single=152, n_multi=0)]
+        probs = [p for p in S.config_batch(seed=rank_seed(3, rank), n_single=152, n_multi=0)]
         return probs, "bf16", "profiling case: 152 single-period instances of the batched workload"
     if name == "diff":
-        probs = S.config_diff(seed=4 + 10 * rank, n_single=64, n_multi=0)
+        probs = S.config_diff(seed=rank_seed(4, rank), n_single=64, n_multi=0)
         return probs, "f32", ("differentiation: 64 single-period instances n=3000 k=60, forward to 1e-7 "
                               "relative KKT then the batched adjoint (vector-Jacobian products for alpha, F, D, "
                               "s, q, w0)")
     if name == "single_large":
-        return [S.config_single_large(seed=1 + 10 * rank)], "f32", "single-period n=10000 k=100 m=160, FP32"
+        return [S.config_single_large(seed=rank_seed(1, rank))], "f32", "single-period n=10000 k=100 m=160, FP32"
     if name == "multi":
-        return [S.config_multi(seed=2 + 10 * rank)], "f32", "multi-period T=20 n=5000 k=80, FP32"
-    return [S.config_single_small(seed=0 + 10 * rank)], "f64", "single-period n=500 k=20, FP64"
+        return [S.config_multi(seed=rank_seed(2, rank))], "f32", "multi-period T=20 n=5000 k=80, FP32"
+    return [S.config_single_small(seed=rank_seed(0, rank))], "f64", "single-period n=500 k=20, FP64"
 
 
 def storage_rounded(p, precision):
@@ -176,37 +178,12 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # distributed plumbing (timing only: no collective touches the data path)
 # ---------------------------------------------------------------------------
-def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
-
-
 def dist_init(backend: str):
     import torch.distributed as dist
     ws, rank, _ = dist_env()
     if ws > 1 and not dist.is_initialized():
         dist.init_process_group(backend=backend)
     return dist if ws > 1 else None
-
-
-def max_over_ranks(dist, value: float, device) -> float:
-    if dist is None:
-        return value
-    import torch
-    t = torch.tensor([value], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
-
-
-def sum_over_ranks(dist, value: float, device) -> float:
-    if dist is None:
-        return value
-    import torch
-    t = torch.tensor([value], dtype=torch.float64, device=device)
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
 
 
 # ---------------------------------------------------------------------------
