@@ -20,7 +20,7 @@ constexpr int kStallChecks = 48;       // checks without halving the KKT before 
 
 constexpr int kStages = 3;             // bulk-copy ring stages per CTA
 constexpr int kMaxTileBytes = 48 * 1024;
-constexpr int kSmemLimit = 227 * 1024 - 2048;   // dynamic shared memory per CTA we allow ourselves
+constexpr int kSmemLimit = 227 * 1024 - 4096;   // dynamic shared memory per CTA we allow ourselves (static use ~2 KB)
 
 // Panel tiling: the rows of F^T (k, padded to kp) and of A (m, padded to mp)
 // form one panel of Rp = kp + mp rows; the assets are cut into tiles of CH.

@@ -332,6 +332,29 @@ __device__ __forceinline__ bool trade_multiplier(double t, double inv_sigma, dou
     return true;
 }
 
+// The multiplier form in FP32 throughout (t, 1/sigma, c1, c2 already FP32):
+// returns true on the live branch with y = phi'(z) in y_live.
+__device__ __forceinline__ bool trade_multiplier_f(float t, float g, float c1, float c2, double d, float& y_live) {
+    const float a = fabsf(t) - g * c1;
+    if (!(a > 0.f)) return false;
+    float deriv;
+    const float gc = g * c2;
+    if (gc <= 0.f) {
+        deriv = c1;
+    } else if (d == 1.5) {
+        const float beta = 1.5f * gc;
+        const float rho = 2.f * a / (beta + sqrtf(beta * beta + 4.f * a));
+        deriv = c1 + 1.5f * c2 * rho;
+    } else if (d == 2.0) {
+        deriv = c1 + 2.f * c2 * (a / (1.f + 2.f * gc));
+    } else {
+        const double r = fabs(prox_cost((double)t, (double)g, (double)c1, (double)c2, d));
+        deriv = c1 + (float)(d * (double)c2 * pow(r, d - 1.0));
+    }
+    y_live = t < 0.f ? -deriv : deriv;
+    return true;
+}
+
 // ---------------------------------------------------------------------------
 // per-CTA context
 // ---------------------------------------------------------------------------
@@ -569,6 +592,57 @@ __device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, c
     __syncthreads();
 }
 
+// Multi-period reduce pass of the FP32-increment iteration: the staged vectors
+// come from the pair buffer (x_bar, x+) in FP32: A rows take (x_bar, x+), F
+// rows (x+ - c, x_bar - c).
+template <int PCT, class M, class S>
+__device__ void reduce_pairs_t(Ctx<M, S>& c, int p0, int pc, const float2* vp) {
+    const int CH = c.I.CH, Rp = c.I.Rp;
+    const int m = c.m, k = c.k, np = c.np, n = c.n;
+    const int Lr = 2 * m + 2 * k;
+    const size_t tile_elems = (size_t)Rp * CH;
+    const unsigned bytes = (unsigned)(tile_elems * sizeof(S));
+    float* st = (float*)c.stage;  // [4][PCT][CH]
+    for (int e = c.tid; e < pc * Lr; e += kThreads) c.vpart[e] = 0;
+    const int nt = c.t1 - c.t0;
+    for (int j = 0; j < nt && j < kStages; ++j) pipe_issue(c.pipe, c.I.PR + (size_t)(c.t0 + j) * tile_elems, bytes);
+    for (int j = 0; j < nt; ++j) {
+        const int t = c.t0 + j;
+        const int ib = t * CH;
+        const int cnt = min(CH, n - ib);
+        for (int e = c.tid; e < PCT * CH; e += kThreads) {
+            const int q = e / CH, ii = e % CH;
+            float xb = 0.f, xn = 0.f, cf = 0.f;
+            if (q < pc && ii < cnt) {
+                const int i = ib + ii;
+                const float2 pr = vp[(size_t)(p0 + q) * np + i];
+                xb = pr.x;
+                xn = pr.y;
+                cf = (float)c.I.cen[i];
+            }
+            st[e] = xb;
+            st[PCT * CH + e] = xn;
+            st[2 * PCT * CH + e] = xn - cf;
+            st[3 * PCT * CH + e] = xb - cf;
+        }
+        const S* tile = (const S*)pipe_wait(c.pipe);
+        __syncthreads();
+        reduce_tile<PCT, float>(c, tile, st, st + PCT * CH, st + 2 * PCT * CH, st + 3 * PCT * CH, cnt, pc, true);
+        __syncthreads();
+        pipe_pop(c.pipe);
+        if (j + kStages < nt) pipe_issue(c.pipe, c.I.PR + (size_t)(t + kStages) * tile_elems, bytes);
+    }
+    __syncthreads();
+}
+
+template <class M, class S>
+__device__ void reduce_chunk_pairs(Ctx<M, S>& c, int p0, int pc, const float2* vp) {
+    if (pc <= 1) reduce_pairs_t<1>(c, p0, pc, vp);
+    else if (pc <= 2) reduce_pairs_t<2>(c, p0, pc, vp);
+    else if (pc <= 4) reduce_pairs_t<4>(c, p0, pc, vp);
+    else reduce_pairs_t<8>(c, p0, pc, vp);
+}
+
 // ---------------------------------------------------------------------------
 // Single-period fused pass (elementwise prox + Halpern + reduce): each PR tile
 // arrives together with its assets' x, x0, y_D, y_D0, w0 (FP64) and c1, c2
@@ -619,31 +693,65 @@ __device__ void reduce_fused_single(Ctx<M, S>& c, double hlA, double hlB, double
         const M* sc2 = (const M*)(stg + off[7]);
         for (int ii = c.tid; ii < cnt; ii += kThreads) {
             const int i = ib + ii;
-            const double vv = c.I.v[i];
-            const double av = fabs(vv) - theta;
-            const double xb = av > 0 ? (vv < 0 ? -av : av) : 0.0;
-            const double xc = sx[ii];
-            const double xn = hlA * xb + hlB * xc + hlC * sx0[ii];
-            const double dxe = 2.0 * xb - xc;          // (Delta (2 x_bar - x))_1
-            const double b = -sw0[ii];
-            const double yd = syd[ii];
-            const double pD = yd + sD * dxe;
-            const double tt = pD * inv_sD + b;
-            M ylive;
-            const double ydb = trade_multiplier<M>(tt, inv_sD, (double)sc1[ii], (double)sc2[ii], dexp, ylive)
-                                   ? (double)ylive
-                                   : pD + sD * b;
-            const double ydn = hlA * ydb + hlB * yd + hlC * syd0[ii];
-            c.I.xn[i] = xn;
-            c.I.yDn[i] = ydn;
-            if (check) {
-                c.I.xb[i] = xb;
-                c.I.yDb[i] = ydb;
-                rloc[0] += (xc - xb) * (xc - xb);
-                rloc[1] += (yd - ydb) * (yd - ydb);
+            if constexpr (std::is_same<M, float>::value) {
+                // FP32 increments on the FP64 state (see the multi-period pass)
+                const float fA = (float)hlA, fC = (float)hlC, fsD = (float)sD, finv = (float)inv_sD;
+                const float2 vu = ((const float2*)c.I.v)[i];
+                const double xc = sx[ii];
+                const float th = (float)theta;
+                const float av = fabsf(vu.x) - th;
+                float d1, xbf = 0.f;
+                if (av > 0.f) {
+                    d1 = vu.y - (vu.x < 0.f ? -th : th);
+                    xbf = vu.x < 0.f ? -av : av;
+                } else {
+                    d1 = -(float)xc;
+                }
+                const double xn = xc + (double)(fA * d1 + fC * (float)(sx0[ii] - xc));
+                const float zz = (float)(xc - sw0[ii]) + 2.f * d1;   // (x - w0) + 2 (x_bar - x)
+                const double yd = syd[ii];
+                const float ydf = (float)yd;
+                const float tf = ydf * finv + zz;
+                float yl, dy;
+                if (trade_multiplier_f(tf, finv, sc1[ii], sc2[ii], dexp, yl)) dy = yl - ydf;
+                else dy = fsD * zz;
+                c.I.xn[i] = xn;
+                c.I.yDn[i] = yd + (double)(fA * dy + fC * (float)(syd0[ii] - yd));
+                if (check) {
+                    c.I.xb[i] = av > 0.f ? xc + (double)d1 : 0.0;   // exact zeros off the support
+                    c.I.yDb[i] = yd + (double)dy;
+                    rloc[0] += (double)d1 * (double)d1;
+                    rloc[1] += (double)dy * (double)dy;
+                }
+                st[ii] = xbf;
+                st[CH + ii] = (float)xn;
+            } else {
+                const double vv = c.I.v[i];
+                const double av = fabs(vv) - theta;
+                const double xb = av > 0 ? (vv < 0 ? -av : av) : 0.0;
+                const double xc = sx[ii];
+                const double xn = hlA * xb + hlB * xc + hlC * sx0[ii];
+                const double dxe = 2.0 * xb - xc;          // (Delta (2 x_bar - x))_1
+                const double b = -sw0[ii];
+                const double yd = syd[ii];
+                const double pD = yd + sD * dxe;
+                const double tt = pD * inv_sD + b;
+                M ylive;
+                const double ydb = trade_multiplier<M>(tt, inv_sD, (double)sc1[ii], (double)sc2[ii], dexp, ylive)
+                                       ? (double)ylive
+                                       : pD + sD * b;
+                const double ydn = hlA * ydb + hlB * yd + hlC * syd0[ii];
+                c.I.xn[i] = xn;
+                c.I.yDn[i] = ydn;
+                if (check) {
+                    c.I.xb[i] = xb;
+                    c.I.yDb[i] = ydb;
+                    rloc[0] += (xc - xb) * (xc - xb);
+                    rloc[1] += (yd - ydb) * (yd - ydb);
+                }
+                st[ii] = (M)xb;
+                st[CH + ii] = (M)xn;
             }
-            st[ii] = (M)xb;
-            st[CH + ii] = (M)xn;
         }
         __syncthreads();
         // A rows: (x_bar, x+); F rows: (x+, x_bar)
@@ -823,9 +931,18 @@ __device__ void expand_main_single(Ctx<M, S>& c, double tau, double kap, const M
         auto epi = [&](int i, int p, double aF, double aA) {
             const int ii = i - ib;
             const double xv = sx[ii];
-            const M gf = -sal[ii] + (M)2 * kapm * ((M)aF + sdp[ii] * (M)xv);
-            const M kt = (M)aA + (M)syd[ii];
-            v[i] = xv - tau * (double)(gf + kt);
+            if constexpr (std::is_same<M, float>::value) {
+                // FP32 step u and v = x + u as a pair (the FP32-increment iteration)
+                const float xf = (float)xv;
+                const float gf = -sal[ii] + 2.f * kapm * ((float)aF + sdp[ii] * xf);
+                const float kt = (float)aA + (float)syd[ii];
+                const float u = -(float)tau * (gf + kt);
+                ((float2*)v)[i] = make_float2(xf + u, u);
+            } else {
+                const M gf = -sal[ii] + (M)2 * kapm * ((M)aF + sdp[ii] * (M)xv);
+                const M kt = (M)aA + (M)syd[ii];
+                v[i] = xv - tau * (double)(gf + kt);
+            }
         };
         expand_tile<1, M>(c, tile, ib, cnt, 0, 1, wF, wA, epi);
         __syncthreads();
@@ -848,8 +965,8 @@ __device__ void expand_main_single(Ctx<M, S>& c, double tau, double kap, const M
 // per-warp partials are added in warp order (deterministic).
 // Returns the number of rounds (passes over v).
 // ---------------------------------------------------------------------------
-template <class M, class S>
-__device__ int l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const double* vv, double* th_out,
+template <class V, class M, class S>
+__device__ int l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const V* vv, double* th_out,
                              double* th_warm) {
     const int P = c.P, np = c.np;
     float* slotS = (float*)c.vpart;     // [kWarps][P][2]  (hi, lo)
@@ -873,16 +990,35 @@ __device__ int l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const double* 
     for (int round = 0; round < kMaxRounds; ++round) {
         for (int p = pstart; p < P; p += pstep) {
             if (done_s[p]) continue;
-            const double* vp = vv + (size_t)p * np;
+            const V* vp = vv + (size_t)p * np;
             const double t = t_s[p];
-            double sd = 0;
             int nd = 0;
-            for (int i = istart; i < c.i1; i += istep) {
-                const double a = fabs(vp[i]);
-                if (a > t) { sd += a; nd += 1; }
+            float hi, lo;
+            if constexpr (std::is_same<V, double>::value) {
+                double sd = 0;
+                for (int i = istart; i < c.i1; i += istep) {
+                    const double a = fabs(vp[i]);
+                    if (a > t) { sd += a; nd += 1; }
+                }
+                hi = (float)sd;
+                lo = (float)(sd - (double)hi);
+            } else {
+                // FP32 entries (v.x), compared with the rounded threshold and
+                // summed as an error-free double-float pair
+                const float tf = (float)t;
+                hi = 0.f;
+                lo = 0.f;
+                for (int i = istart; i < c.i1; i += istep) {
+                    const float a = fabsf(vp[i].x);
+                    if (a > tf) {
+                        float sum, err;
+                        two_sum(hi, a, sum, err);
+                        hi = sum;
+                        lo += err;
+                        nd += 1;
+                    }
+                }
             }
-            float hi = (float)sd;
-            float lo = (float)(sd - (double)hi);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
@@ -981,6 +1117,9 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
     cg::cluster_group cl = cg::this_cluster();
     const int G = (int)cl.num_blocks();
     const int g = (int)cl.block_rank();
+    // FP32 increments on the FP64 state (FP32 and BF16 modes); FP64 mode keeps
+    // every elementwise operation in FP64
+    constexpr bool kIncr = std::is_same<M, float>::value;
     __shared__ int next_s;
     __shared__ int pipe_err_s;
     Pipe pipe;
@@ -1181,6 +1320,21 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             // (2) expand: v = x - tau (grad f(x) + K^T y)
             if constexpr (PCMAX == 1) {
                 expand_main_single(c, tau, kap, c.om, c.yAm);
+            } else if constexpr (kIncr) {
+                // FP32 step u = -tau (grad f + K^T y) and v = x + u, stored as a pair
+                const double* x = c.I.x;
+                const double* yD = c.I.yD;
+                float2* v2 = (float2*)c.I.v;
+                const float kapf = (float)kap, tauf = (float)tau;
+                expand_pass<M, PCMAX>(c, P, c.om, c.yAm, [&](int i, int p, double aF, double aA) {
+                    const size_t o = (size_t)p * np + i;
+                    const float xf = (float)x[o];
+                    const float gf = -(float)c.I.alpha[o] +
+                                     2.f * kapf * ((float)aF + (float)c.I.Dp[o] * (xf - (float)c.I.cen[i]));
+                    const float kt = (float)aA + (float)yD[o] - ((p + 1 < R) ? (float)yD[o + np] : 0.f);
+                    const float u = -tauf * (gf + kt);
+                    v2[o] = make_float2(xf + u, u);
+                });
             } else {
                 const double* x = c.I.x;
                 const double* yD = c.I.yD;
@@ -1198,12 +1352,77 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             __syncthreads();
             lap(1);
             // (3) thresholds of the l1 projection
-            th_rounds += l1_thresholds(cl, c, c.I.v, c.theta, c.thprev);
+            if constexpr (kIncr)
+                th_rounds += l1_thresholds(cl, c, (const float2*)c.I.v, c.theta, c.thprev);
+            else
+                th_rounds += l1_thresholds(cl, c, (const double*)c.I.v, c.theta, c.thprev);
             lap(2);
             // (4) elementwise: x_bar, y_D bar, Halpern combination, residual parts
             //     (fused into the reduce pass for a single period)
             double rloc[2] = {0, 0};
-            if constexpr (PCMAX != 1) {
+            if constexpr (PCMAX != 1 && kIncr) {
+                // FP32 increments: with d1 = x_bar - x (from u and theta) and
+                // d0 = x0 - x, x+ = x + hlA d1 + hlC d0; the trade residual of row r is
+                // (Delta x + b)_r + 2 (d1_r - d1_{r-1}) from FP64 differences; the dual
+                // update y+ = y + hlA (y_bar - y) + hlC (y0 - y).  (x_bar, x+) in FP32
+                // replace (v, u) in the pair buffer for the reduce pass.
+                const double* x = c.I.x;
+                float2* v2 = (float2*)c.I.v;
+                const float fA = (float)hlA, fC = (float)hlC, fsD = (float)sD, finv = (float)inv_sD;
+                for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
+                    const double w0 = c.I.w0[i];
+                    const double wt = c.I.multi ? c.I.cen[i] : 0.0;
+                    double x_prev = 0.0;
+                    float d1_prev = 0.f;
+                    for (int r = 0; r < R; ++r) {
+                        float d1 = 0.f;
+                        double xc = 0.0;
+                        if (r < P) {
+                            const size_t o = (size_t)r * np + i;
+                            const float2 vu = v2[o];
+                            xc = x[o];
+                            const float th = (float)c.theta[r];
+                            const float av = fabsf(vu.x) - th;
+                            float xbf = 0.f;
+                            if (av > 0.f) {
+                                d1 = vu.y - (vu.x < 0.f ? -th : th);
+                                xbf = vu.x < 0.f ? -av : av;
+                            } else {
+                                d1 = -(float)xc;
+                            }
+                            const float d0 = (float)(c.I.x0[o] - xc);
+                            const double xn = xc + (double)(fA * d1 + fC * d0);
+                            c.I.xn[o] = xn;
+                            v2[o] = make_float2(xbf, (float)xn);
+                            if (check) {
+                                c.I.xb[o] = av > 0.f ? xc + (double)d1 : 0.0;   // exact zeros off the support
+                                rloc[0] += (double)d1 * (double)d1;
+                            }
+                        }
+                        // (Delta x + b)_r in FP64, then the FP32 correction 2 (d1_r - d1_{r-1})
+                        const double dxb = (r < P ? xc : 0.0) - x_prev + (r == 0 ? -w0 : 0.0) +
+                                           ((c.I.multi && r == R - 1) ? wt : 0.0);
+                        const float zz = (float)dxb + 2.f * (d1 - d1_prev);
+                        x_prev = xc;
+                        d1_prev = d1;
+                        const size_t orr = (size_t)r * np + i;
+                        const double yd = c.I.yD[orr];
+                        const float ydf = (float)yd;
+                        const float tf = ydf * finv + zz;
+                        float yl, dy;
+                        if (trade_multiplier_f(tf, finv, (float)c.I.c1[orr], (float)c.I.c2[orr], dexp, yl))
+                            dy = yl - ydf;
+                        else
+                            dy = fsD * zz;
+                        const float d0y = (float)(c.I.yD0[orr] - yd);
+                        c.I.yDn[orr] = yd + (double)(fA * dy + fC * d0y);
+                        if (check) {
+                            c.I.yDb[orr] = yd + (double)dy;
+                            rloc[1] += (double)dy * (double)dy;
+                        }
+                    }
+                }
+            } else if constexpr (PCMAX != 1) {
                 const double* x = c.I.x;
                 const double* v = c.I.v;
                 for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
@@ -1249,6 +1468,8 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                 const int pc = min(kPC, P - p0);
                 if constexpr (PCMAX == 1)
                     reduce_fused_single(c, hlA, hlB, hlC, sD, inv_sD, dexp, check, rloc);
+                else if constexpr (kIncr)
+                    reduce_chunk_pairs(c, p0, pc, (const float2*)c.I.v);
                 else
                     reduce_chunk<PCMAX>(c, p0, pc, c.I.xb, c.I.xn, c.I.xn, (const double*)nullptr, true);
                 team_reduce<false>(cl, c.vpart, c.vout, pc * Lr, G, g);
@@ -1403,7 +1624,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             __syncthreads();
             // stationarity residual ||x_bar - Proj(q)||  (thresholds warm-started
             // from the previous check)
-            l1_thresholds(cl, c, c.I.v, c.theta, c.thq);
+            l1_thresholds(cl, c, (const double*)c.I.v, c.theta, c.thq);
             double dr[1] = {0};
             for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
                 for (int p = 0; p < P; ++p) {
