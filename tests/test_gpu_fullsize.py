@@ -1,0 +1,79 @@
+"""Parity at the benchmark configurations' full sizes (GPU).
+
+* the large single-period configuration (n = 10000, k = 100, m = 160, FP32)
+  and the multi-period configuration (T = 20, n = 5000, k = 80, FP32), each
+  solved alone and compared with the oracle on the whole portfolio;
+* the batched configuration (576 instances, BF16 panels) in the launch
+  configuration the benchmark times (one packed batch, CUDA graph replay):
+  every instance must converge, and sampled instances are compared with the
+  oracle one by one.
+
+The solves run to 2e-7 relative KKT for the same reason as the small parity
+tests (a 1e-6 point is not certified within 1e-5 of w*).  Bars:
+|w - w*|_inf <= 1e-5, relative objective gap <= 1e-6 (relative to the
+magnitude of the objective's terms), the solver's own relative KKT <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import Scaled
+from oracle.kkt import term_scale
+from paper_2604_22625_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+TOL_SOLVE = 2e-7
+
+
+@pytest.fixture(scope="module")
+def api():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2604_22625_gb300 import api as _api
+    from paper_2604_22625_gb300.build import build
+    build()
+    return _api
+
+
+def _check(prob, x, info):
+    assert info["status_name"] == "converged", info
+    assert info["rel_kkt"] <= 1e-6
+    ref = oracle.solve(prob)
+    sc = Scaled(prob)
+    x = np.asarray(x, dtype=np.float64).reshape(sc.P, sc.n)
+    err = float(np.max(np.abs(x - ref.x)))
+    gap = abs(sc.objective(x) - ref.obj) / max(abs(ref.obj), term_scale(sc, ref.x))
+    assert err <= 1e-5, (prob.tag, err)
+    assert gap <= 1e-6, (prob.tag, gap)
+
+
+def test_single_large_full(api):
+    prob = S.config_single_large().rounded(np.float32)
+    sol = api.solve(prob, precision="f32", tol=TOL_SOLVE)
+    _check(prob, sol.x, sol.info)
+
+
+def test_multi_full(api):
+    prob = S.config_multi().rounded(np.float32)
+    sol = api.solve(prob, precision="f32", tol=TOL_SOLVE)
+    _check(prob, sol.x, sol.info)
+
+
+def test_batch_full_sampled(api):
+    import torch
+    probs = S.config_batch()
+    br = api.BatchRunner(probs, precision="bf16", tol=TOL_SOLVE)
+    br.capture()
+    br.replay()
+    torch.cuda.synchronize()
+    infos = br.results()
+    assert all(i["status_name"] == "converged" and i["rel_kkt"] <= 1e-6 for i in infos)
+    ws = br.portfolios()
+    rng = np.random.default_rng(11)
+    singles = [i for i, p in enumerate(probs) if int(p.T) < 2]
+    multis = sorted([i for i, p in enumerate(probs) if int(p.T) >= 2], key=lambda i: probs[i].n * probs[i].T)
+    picks = list(rng.choice(singles, 3, replace=False)) + [multis[0]]
+    for i in picks:
+        _check(probs[i].with_F_rounded_bf16(), ws[i], infos[i])
