@@ -50,7 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="batch",
-                    choices=["batch", "single_large", "multi", "single_small", "batch_profile", "diff"])
+                    choices=["batch", "single_large", "multi", "single_small", "batch_profile", "multi_profile",
+                             "diff"])
     ap.add_argument("--max-iter", type=int, default=0, help="iteration cap (profiling runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="call ff_solve_batch directly instead of "
@@ -75,6 +76,10 @@ def make_workload(name: str, rank: int):
     if name == "batch_profile":
         probs = [p for p in S.config_batch(seed=rank_seed(3, rank), n_single=152, n_multi=0)]
         return probs, "bf16", "profiling case: 152 single-period instances of the batched workload"
+    if name == "multi_profile":
+        allp = S.config_batch(seed=rank_seed(3, rank))
+        probs = sorted([p for p in allp if int(p.T) >= 2], key=lambda p: -p.n * p.T)[:8]
+        return probs, "bf16", "profiling case: the 8 largest multi-period instances of the batched workload"
     if name == "diff":
         probs = S.config_diff(seed=rank_seed(4, rank), n_single=64, n_multi=0)
         return probs, "f32", ("differentiation: 64 single-period instances n=3000 k=60, forward to 1e-7 "

@@ -186,7 +186,7 @@ __device__ __forceinline__ void pipe_issue(Pipe& pp, const void* src, unsigned b
     ++pp.inflight;
 }
 
-// Issue up to 8 copies into the tail stage that complete on its one barrier:
+// Issue nc copies into the tail stage that complete on its one barrier:
 // copy q moves bytes[q] from src[q] to the stage offset off[q].
 __device__ __forceinline__ void pipe_issue_n(Pipe& pp, int nc, const void* const* src, const unsigned* off,
                                              const unsigned* bytes) {
@@ -378,6 +378,26 @@ struct Ctx {
 // Sum (or max) of part[0..K) over the team; result in out[0..K) of every CTA.
 // The G remote loads of an entry are issued together and added in rank order,
 // so every CTA receives bit-identical totals.
+// Entries [0, ksum) are summed, entries [ksum, K) take the maximum.
+__device__ void team_reduce_mixed(cg::cluster_group& cl, double* part, double* out, int K, int ksum, int G, int g) {
+    cl.sync();
+    const int per = (K + G - 1) / G;
+    const int lo = g * per;
+    const int hi = min(K, lo + per);
+    for (int idx = lo + (int)threadIdx.x; idx < hi; idx += blockDim.x) {
+        const bool mx = idx >= ksum;
+        double v[kMaxCluster];
+#pragma unroll
+        for (int q = 0; q < kMaxCluster; ++q)
+            v[q] = (q < G) ? cl.map_shared_rank(part, q)[idx] : (mx ? -INFINITY : 0.0);
+        double s = v[0];
+#pragma unroll
+        for (int q = 1; q < kMaxCluster; ++q) s = mx ? fmax(s, v[q]) : s + v[q];
+        for (int q = 0; q < G; ++q) cl.map_shared_rank(out, q)[idx] = s;
+    }
+    cl.sync();
+}
+
 template <bool MAX>
 __device__ void team_reduce(cg::cluster_group& cl, double* part, double* out, int K, int G, int g) {
     cl.sync();
@@ -971,6 +991,7 @@ __device__ int l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const V* vv, d
     const int P = c.P, np = c.np;
     float* slotS = (float*)c.vpart;     // [kWarps][P][2]  (hi, lo)
     int* slotN = (int*)c.vout;          // [kWarps][P]
+    float* slotB = (float*)(slotN + kWarps * P);   // [kWarps][P][2] bracket (max inactive, min active)
     __shared__ int done_s[64];
     __shared__ double t_s[64];
     __shared__ int nprev_s[64];
@@ -993,21 +1014,31 @@ __device__ int l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const V* vv, d
             const V* vp = vv + (size_t)p * np;
             const double t = t_s[p];
             int nd = 0;
-            float hi, lo;
+            float hi, lo, bl, bh;   // sum pair; bracket: largest |v| <= t, smallest |v| > t
             if constexpr (std::is_same<V, double>::value) {
-                double sd = 0;
+                double sd = 0, l = -1.0, h = INFINITY;
                 for (int i = istart; i < c.i1; i += istep) {
                     const double a = fabs(vp[i]);
-                    if (a > t) { sd += a; nd += 1; }
+                    if (a > t) { sd += a; nd += 1; h = fmin(h, a); }
+                    else l = fmax(l, a);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    l = fmax(l, __shfl_xor_sync(0xffffffffu, l, o));
+                    h = fmin(h, __shfl_xor_sync(0xffffffffu, h, o));
                 }
                 hi = (float)sd;
                 lo = (float)(sd - (double)hi);
+                bl = __double2float_ru(l);   // rounded outward: the bracket test stays conservative
+                bh = __double2float_rd(h);
             } else {
                 // FP32 entries (v.x), compared with the rounded threshold and
                 // summed as an error-free double-float pair
                 const float tf = (float)t;
                 hi = 0.f;
                 lo = 0.f;
+                bl = -1.f;
+                bh = INFINITY;
                 for (int i = istart; i < c.i1; i += istep) {
                     const float a = fabsf(vp[i].x);
                     if (a > tf) {
@@ -1016,14 +1047,22 @@ __device__ int l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const V* vv, d
                         hi = sum;
                         lo += err;
                         nd += 1;
+                        bh = fminf(bh, a);
+                    } else {
+                        bl = fmaxf(bl, a);
                     }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    bl = fmaxf(bl, __shfl_xor_sync(0xffffffffu, bl, o));
+                    bh = fminf(bh, __shfl_xor_sync(0xffffffffu, bh, o));
                 }
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
-                const float bh = __shfl_xor_sync(0xffffffffu, hi, o);
-                const float bl = __shfl_xor_sync(0xffffffffu, lo, o);
-                df_add(hi, lo, bh, bl);
+                const float sh = __shfl_xor_sync(0xffffffffu, hi, o);
+                const float sl = __shfl_xor_sync(0xffffffffu, lo, o);
+                df_add(hi, lo, sh, sl);
             }
             const int nsum = __reduce_add_sync(0xffffffffu, nd);
             if (c.lane == 0) {
@@ -1031,22 +1070,28 @@ __device__ int l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const V* vv, d
                 slotS[2 * slot] = hi;
                 slotS[2 * slot + 1] = lo;
                 slotN[slot] = nsum;
+                slotB[2 * slot] = bl;
+                slotB[2 * slot + 1] = bh;
             }
         }
         __syncthreads();
         for (int p = c.tid; p < P; p += kThreads) {
-            double sv = 0, nn = 0;
+            double sv = 0, nn = 0, bl = -1.0, bh = INFINITY;
             if (!done_s[p]) {
                 for (int w = 0; w < nw; ++w) {
                     const int slot = wpp ? p : (w * P + p);
                     sv += (double)slotS[2 * slot] + (double)slotS[2 * slot + 1];
                     nn += (double)slotN[slot];
+                    bl = fmax(bl, (double)slotB[2 * slot]);
+                    bh = fmin(bh, (double)slotB[2 * slot + 1]);
                 }
             }
             c.spart[2 * p] = sv;
             c.spart[2 * p + 1] = nn;
+            c.spart[2 * P + 2 * p] = bl;
+            c.spart[2 * P + 2 * p + 1] = -bh;
         }
-        team_reduce<false>(cl, c.spart, c.sout, 2 * P, c.G, c.g);
+        team_reduce_mixed(cl, c.spart, c.sout, 4 * P, 2 * P, c.G, c.g);
         if (c.tid == 0) {
             for (int p = 0; p < P; ++p) {
                 if (done_s[p]) continue;
@@ -1064,6 +1109,15 @@ __device__ int l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const V* vv, d
                     continue;
                 }
                 double tn = (Sv - 1.0) / (double)(Nv > 0 ? Nv : 1);
+                // the Newton point keeps the active set of t (no |v| between t and
+                // tn): S is linear on the bracket and tn is the root, in one pass
+                const double blo = c.sout[2 * P + 2 * p], bhi = -c.sout[2 * P + 2 * p + 1];
+                const double tcmp = std::is_same<V, double>::value ? tn : (double)(float)tn;
+                if (Nv > 0 && tn > 0.0 && blo <= tcmp && tcmp < bhi) {
+                    th_out[p] = tn;
+                    done_s[p] = 1;
+                    continue;
+                }
                 if (tn <= 0.0) {                               // step from above past 0: test 0
                     tn = 0.0;
                     nprev_s[p] = -1;
