@@ -88,6 +88,8 @@ size_t inst_bytes(const Sizes& s, int omega_diag, int precision) {
     b += 5 * a256((size_t)s.P * s.np * r);                  // x, x0, xb, xn, v
     b += 4 * a256((size_t)s.R * s.np * r);                  // yD, yD0, yDb, yDn
     b += a256((size_t)s.P * s.m * r + 16);                  // yA0
+    b += a256((size_t)s.R * s.np * 4);                      // yDf
+    b += a256((size_t)s.np * 4);                            // cenf
     b += 2 * a256((size_t)s.np * r);                        // power-iteration vectors
     return b;
 }
@@ -236,6 +238,7 @@ __device__ void repack_one(const ff_problem& p, const Inst<M, S>& I, double lam2
         }
         ((double*)I.w0)[i] = (double)(in ? (double)w0[i] : 0.0);
         ((double*)I.cen)[i] = (double)((in && I.multi) ? (double)wT[i] : 0.0);
+        ((float*)I.cenf)[i] = (float)((in && I.multi) ? (double)wT[i] : 0.0);
         if (I.multi) ((double*)I.alphaT)[i] = (double)(in ? (double)al[(size_t)P * n + i] : 0.0);
     }
 }
@@ -288,6 +291,8 @@ Inst<M, S> carve(const ff_problem& p, const Sizes& s, unsigned char*& cur, void*
     I.yDb = (double*)take((size_t)s.R * s.np * r);
     I.yDn = (double*)take((size_t)s.R * s.np * r);
     I.yA0 = (double*)take((size_t)s.P * s.m * r + 16);
+    I.yDf = (float*)take((size_t)s.R * s.np * 4);
+    I.cenf = (const float*)take((size_t)s.np * 4);
     I.pv1 = (double*)take((size_t)s.np * r);
     I.pv2 = (double*)take((size_t)s.np * r);
     I.kappa = p.lambda1 * p.GMV;

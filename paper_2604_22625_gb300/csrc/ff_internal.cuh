@@ -71,6 +71,8 @@ struct Inst {
     // iterate storage (workspace)
     double *x, *x0, *xb, *xn, *v;      // P x np
     double *yD, *yD0, *yDb, *yDn;      // R x np
+    float* yDf;                        // R x np   FP32 copy of y_D (multi-period FP32 increments)
+    const float* cenf;                 // np       FP32 copy of the centre
     double* yA0;                       // P x m anchor of the replicated y_A
     double *pv1, *pv2;                 // np power-iteration vectors
     // outputs

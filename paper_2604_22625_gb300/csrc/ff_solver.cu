@@ -499,73 +499,104 @@ template <class M> struct RowLoad<M, double> {
 // first lane (one owner per entry: no races, fixed order).  Null vectors give
 // zeros.
 // ---------------------------------------------------------------------------
-// Products of one PR tile with the staged vectors, added into vpart (FP64).
-// sv0A/sv1A feed the A rows, sv0F/sv1F the F rows ([PCT][CH] each).
-template <int PCT, class AT, class M, class S>
-__device__ __forceinline__ void reduce_tile(Ctx<M, S>& c, const S* tile, const AT* sv0A, const AT* sv1A,
-                                            const AT* sv0F, const AT* sv1F, int cnt, int pc, bool has1) {
+// Products of one PR tile with the staged vectors.  sv0A/sv1A feed the A
+// rows, sv0F/sv1F the F rows ([PCT][CH] each).  The products accumulate in
+// acc (AT, per thread) across consecutive tiles; reduce_flush combines the
+// lanes of each row group by shuffles and adds the sums into vpart in FP64
+// (one owner per entry, fixed order) and clears acc.
+template <int PCT, class AT> struct ReduceAcc {
+    AT a[4][2][PCT];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < PCT; ++q) { a[r][0][q] = 0; a[r][1][q] = 0; }
+    }
+};
+
+struct ReduceMap {
+    int na, grp, lane_a, r0;
+    bool active, isA;
+};
+
+template <class M, class S>
+__device__ __forceinline__ ReduceMap reduce_map(const Ctx<M, S>& c) {
     constexpr int RPT = 4;
-    const int CH = c.I.CH, Rp = c.I.Rp, kp = c.I.kp;
-    const int m = c.m, k = c.k;
-    const int Lr = 2 * m + 2 * k;
-    const int ngr = Rp / RPT;
+    ReduceMap mp;
+    const int ngr = c.I.Rp / RPT;
     int na = 1;
     while (na < 32 && ngr * na * 2 <= kThreads) na *= 2;
-    const int grp = c.tid / na, lane_a = c.tid % na;
-    const bool active = grp < ngr;
-    const int r0 = grp * RPT;
-    const bool isA = r0 >= kp;
-    AT acc[RPT][2][PCT];
-#pragma unroll
-    for (int r = 0; r < RPT; ++r)
-#pragma unroll
-        for (int q = 0; q < PCT; ++q) { acc[r][0][q] = 0; acc[r][1][q] = 0; }
-    if (active) {
-        const AT* sv0 = isA ? sv0A : sv0F;
-        const AT* sv1 = isA ? sv1A : sv1F;
-        for (int ii = lane_a; ii < cnt; ii += na) {
+    mp.na = na;
+    mp.grp = c.tid / na;
+    mp.lane_a = c.tid % na;
+    mp.active = mp.grp < ngr;
+    mp.r0 = mp.grp * RPT;
+    mp.isA = mp.r0 >= c.I.kp;
+    return mp;
+}
+
+template <int PCT, class AT, class M, class S>
+__device__ __forceinline__ void reduce_tile(Ctx<M, S>& c, const ReduceMap& mp, ReduceAcc<PCT, AT>& acc,
+                                            const S* tile, const AT* sv0A, const AT* sv1A, const AT* sv0F,
+                                            const AT* sv1F, int cnt, bool has1) {
+    constexpr int RPT = 4;
+    const int CH = c.I.CH, Rp = c.I.Rp;
+    if (mp.active) {
+        const AT* sv0 = mp.isA ? sv0A : sv0F;
+        const AT* sv1 = mp.isA ? sv1A : sv1F;
+        for (int ii = mp.lane_a; ii < cnt; ii += mp.na) {
             AT w[RPT];
-            RowLoad<AT, S>::load(tile + (size_t)ii * Rp + r0, w);
+            RowLoad<AT, S>::load(tile + (size_t)ii * Rp + mp.r0, w);
 #pragma unroll
             for (int q = 0; q < PCT; ++q) {
                 const AT x0 = sv0[q * CH + ii];
                 const AT x1 = has1 ? sv1[q * CH + ii] : (AT)0;
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
-                    acc[r][0][q] += w[r] * x0;
-                    acc[r][1][q] += w[r] * x1;
-                }
-            }
-        }
-    }
-    for (int off = na / 2; off > 0; off >>= 1) {
-#pragma unroll
-        for (int r = 0; r < RPT; ++r)
-#pragma unroll
-            for (int q = 0; q < PCT; ++q) {
-                acc[r][0][q] += __shfl_xor_sync(0xffffffffu, acc[r][0][q], off);
-                acc[r][1][q] += __shfl_xor_sync(0xffffffffu, acc[r][1][q], off);
-            }
-    }
-    if (active && lane_a == 0) {
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) {
-            const int row = r0 + r;
-            int o0 = -1, o1 = -1;
-            if (!isA && row < k) { o0 = 2 * m + row; o1 = 2 * m + k + row; }
-            if (isA && row - kp < m) { o0 = row - kp; o1 = m + row - kp; }
-            if (o0 >= 0) {
-#pragma unroll
-                for (int q = 0; q < PCT; ++q) {
-                    if (q < pc) {
-                        c.vpart[q * Lr + o0] += (double)acc[r][0][q];
-                        c.vpart[q * Lr + o1] += (double)acc[r][1][q];
-                    }
+                    acc.a[r][0][q] += w[r] * x0;
+                    acc.a[r][1][q] += w[r] * x1;
                 }
             }
         }
     }
 }
+
+template <int PCT, class AT, class M, class S>
+__device__ __forceinline__ void reduce_flush(Ctx<M, S>& c, const ReduceMap& mp, ReduceAcc<PCT, AT>& acc, int pc) {
+    constexpr int RPT = 4;
+    const int kp = c.I.kp, m = c.m, k = c.k;
+    const int Lr = 2 * m + 2 * k;
+    for (int off = mp.na / 2; off > 0; off >>= 1) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+            for (int q = 0; q < PCT; ++q) {
+                acc.a[r][0][q] += __shfl_xor_sync(0xffffffffu, acc.a[r][0][q], off);
+                acc.a[r][1][q] += __shfl_xor_sync(0xffffffffu, acc.a[r][1][q], off);
+            }
+    }
+    if (mp.active && mp.lane_a == 0) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int row = mp.r0 + r;
+            int o0 = -1, o1 = -1;
+            if (!mp.isA && row < k) { o0 = 2 * m + row; o1 = 2 * m + k + row; }
+            if (mp.isA && row - kp < m) { o0 = row - kp; o1 = m + row - kp; }
+            if (o0 >= 0) {
+#pragma unroll
+                for (int q = 0; q < PCT; ++q) {
+                    if (q < pc) {
+                        c.vpart[q * Lr + o0] += (double)acc.a[r][0][q];
+                        c.vpart[q * Lr + o1] += (double)acc.a[r][1][q];
+                    }
+                }
+            }
+        }
+    }
+    acc.clear();
+}
+
+constexpr int kFlushTiles = 4;   // tiles summed in the matvec precision before an FP64 flush
 
 template <int PCT, class AT, class M, class S>
 __device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, const double* a1,
@@ -580,6 +611,9 @@ __device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, c
     const unsigned bytes = (unsigned)(tile_elems * sizeof(S));
     AT* st = (AT*)c.stage;  // [4][PCT][CH]
     for (int e = c.tid; e < pc * Lr; e += kThreads) c.vpart[e] = 0;
+    const ReduceMap mp = reduce_map(c);
+    ReduceAcc<PCT, AT> acc;
+    acc.clear();
     const int nt = c.t1 - c.t0;
     for (int j = 0; j < nt && j < kStages; ++j) pipe_issue(c.pipe, c.I.PR + (size_t)(c.t0 + j) * tile_elems, bytes);
     for (int j = 0; j < nt; ++j) {
@@ -603,8 +637,9 @@ __device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, c
         }
         const S* tile = (const S*)pipe_wait(c.pipe);
         __syncthreads();
-        reduce_tile<PCT, AT>(c, tile, st, st + PCT * CH, st + (single_fa ? 1 : 2) * PCT * CH,
-                             st + (single_fa ? 0 : 3) * PCT * CH, cnt, pc, has1);
+        reduce_tile<PCT, AT>(c, mp, acc, tile, st, st + PCT * CH, st + (single_fa ? 1 : 2) * PCT * CH,
+                             st + (single_fa ? 0 : 3) * PCT * CH, cnt, has1);
+        if ((j + 1) % kFlushTiles == 0 || j + 1 == nt) reduce_flush<PCT, AT>(c, mp, acc, pc);
         __syncthreads();
         pipe_pop(c.pipe);
         if (j + kStages < nt) pipe_issue(c.pipe, c.I.PR + (size_t)(t + kStages) * tile_elems, bytes);
@@ -624,6 +659,9 @@ __device__ void reduce_pairs_t(Ctx<M, S>& c, int p0, int pc, const float2* vp) {
     const unsigned bytes = (unsigned)(tile_elems * sizeof(S));
     float* st = (float*)c.stage;  // [4][PCT][CH]
     for (int e = c.tid; e < pc * Lr; e += kThreads) c.vpart[e] = 0;
+    const ReduceMap mp = reduce_map(c);
+    ReduceAcc<PCT, float> acc;
+    acc.clear();
     const int nt = c.t1 - c.t0;
     for (int j = 0; j < nt && j < kStages; ++j) pipe_issue(c.pipe, c.I.PR + (size_t)(c.t0 + j) * tile_elems, bytes);
     for (int j = 0; j < nt; ++j) {
@@ -638,7 +676,7 @@ __device__ void reduce_pairs_t(Ctx<M, S>& c, int p0, int pc, const float2* vp) {
                 const float2 pr = vp[(size_t)(p0 + q) * np + i];
                 xb = pr.x;
                 xn = pr.y;
-                cf = (float)c.I.cen[i];
+                cf = c.I.cenf[i];
             }
             st[e] = xb;
             st[PCT * CH + e] = xn;
@@ -647,7 +685,9 @@ __device__ void reduce_pairs_t(Ctx<M, S>& c, int p0, int pc, const float2* vp) {
         }
         const S* tile = (const S*)pipe_wait(c.pipe);
         __syncthreads();
-        reduce_tile<PCT, float>(c, tile, st, st + PCT * CH, st + 2 * PCT * CH, st + 3 * PCT * CH, cnt, pc, true);
+        reduce_tile<PCT, float>(c, mp, acc, tile, st, st + PCT * CH, st + 2 * PCT * CH, st + 3 * PCT * CH, cnt,
+                                true);
+        if ((j + 1) % kFlushTiles == 0 || j + 1 == nt) reduce_flush<PCT, float>(c, mp, acc, pc);
         __syncthreads();
         pipe_pop(c.pipe);
         if (j + kStages < nt) pipe_issue(c.pipe, c.I.PR + (size_t)(t + kStages) * tile_elems, bytes);
@@ -687,6 +727,9 @@ __device__ void reduce_fused_single(Ctx<M, S>& c, double hlA, double hlB, double
     M* st = c.stage;  // [2][CH]: x_bar, x+
     const double theta = c.theta[0];
     for (int e = c.tid; e < Lr; e += kThreads) c.vpart[e] = 0;
+    const ReduceMap mp = reduce_map(c);
+    ReduceAcc<1, M> acc;
+    acc.clear();
     auto issue = [&](int t) {
         const int ib = t * CH;
         const unsigned nv = (unsigned)min(CH, np - ib);
@@ -775,7 +818,8 @@ __device__ void reduce_fused_single(Ctx<M, S>& c, double hlA, double hlB, double
         }
         __syncthreads();
         // A rows: (x_bar, x+); F rows: (x+, x_bar)
-        reduce_tile<1, M>(c, tile, st, st + CH, st + CH, st, cnt, 1, true);
+        reduce_tile<1, M>(c, mp, acc, tile, st, st + CH, st + CH, st, cnt, true);
+        if ((j + 1) % kFlushTiles == 0 || j + 1 == nt) reduce_flush<1, M>(c, mp, acc, 1);
         __syncthreads();
         pipe_pop(c.pipe);
         if (j + kStages < nt) issue(t + kStages);
@@ -860,7 +904,7 @@ __device__ void expand_tile(Ctx<M, S>& c, const S* tile, int ib, int cnt, int p0
         if (ii < cnt) {
 #pragma unroll
             for (int q = 0; q < PCT; ++q)
-                if (q < pc) epi(ib + ii, p0 + q, (double)aF[q], (double)aA[q]);
+                if (q < pc) epi(ib + ii, p0 + q, aF[q], aA[q]);
         }
         return;
     }
@@ -879,7 +923,7 @@ __device__ void expand_tile(Ctx<M, S>& c, const S* tile, int ib, int cnt, int p0
                 sF += red[(((size_t)r * CH + i2) * 2 + 0) * PCT + q];
                 sA += red[(((size_t)r * CH + i2) * 2 + 1) * PCT + q];
             }
-            epi(ib + i2, p0 + q, (double)sF, (double)sA);
+            epi(ib + i2, p0 + q, sF, sA);
         }
     }
     __syncthreads();
@@ -948,7 +992,7 @@ __device__ void expand_main_single(Ctx<M, S>& c, double tau, double kap, const M
         const double* syd = (const double*)(stg + off[2]);
         const M* sal = (const M*)(stg + off[3]);
         const M* sdp = (const M*)(stg + off[4]);
-        auto epi = [&](int i, int p, double aF, double aA) {
+        auto epi = [&](int i, int p, auto aF, auto aA) {
             const int ii = i - ib;
             const double xv = sx[ii];
             if constexpr (std::is_same<M, float>::value) {
@@ -1275,7 +1319,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                 __syncthreads();
                 apply_omega_m(c, c.u, c.om, 1);
                 double nrm[2] = {0, 0};
-                expand_pass<M, PCMAX>(c, 1, c.om, c.yAm, [&](int i, int p, double aF, double aA) {
+                expand_pass<M, PCMAX>(c, 1, c.om, c.yAm, [&](int i, int p, auto aF, auto aA) {
                     const double w1 = aF + c.I.Dmax[i] * v1[i];
                     nrm[0] += w1 * w1;
                     nrm[1] += aA * aA;
@@ -1307,6 +1351,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         const double sA = sig / nA2;
         const double sD = sig / nD2;
         const double inv_sD = 1.0 / sD;
+        const double inv_sA = 1.0 / sA;
         const double rho = prm.rho;
 
         // ---- initial point: w0 (single) / straight line w0 -> w_T (multi) ----
@@ -1321,6 +1366,14 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             for (int r = 0; r < R; ++r) {
                 c.I.yD[(size_t)r * np + i] = 0;
                 c.I.yD0[(size_t)r * np + i] = 0;
+            }
+        }
+        if constexpr (kIncr && PCMAX != 1) {
+            // FP32 views the multi-period expand reads: x in the pair buffer, y_D = 0
+            for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
+                for (int p = 0; p < P; ++p)
+                    ((float2*)c.I.v)[(size_t)p * np + i] = make_float2(0.f, (float)c.I.x[(size_t)p * np + i]);
+                for (int r = 0; r < R; ++r) c.I.yDf[(size_t)r * np + i] = 0.f;
             }
         }
         for (int e = c.tid; e < P * m; e += kThreads) {
@@ -1376,16 +1429,17 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                 expand_main_single(c, tau, kap, c.om, c.yAm);
             } else if constexpr (kIncr) {
                 // FP32 step u = -tau (grad f + K^T y) and v = x + u, stored as a pair
-                const double* x = c.I.x;
-                const double* yD = c.I.yD;
+                // x in FP32 is the second member of the pair buffer (x+ of the last
+                // elementwise pass), y_D in FP32 is its FP32 copy: no conversions
+                const float* yDf = c.I.yDf;
                 float2* v2 = (float2*)c.I.v;
                 const float kapf = (float)kap, tauf = (float)tau;
-                expand_pass<M, PCMAX>(c, P, c.om, c.yAm, [&](int i, int p, double aF, double aA) {
+                expand_pass<M, PCMAX>(c, P, c.om, c.yAm, [&](int i, int p, auto aF, auto aA) {
                     const size_t o = (size_t)p * np + i;
-                    const float xf = (float)x[o];
+                    const float xf = v2[o].y;
                     const float gf = -(float)c.I.alpha[o] +
-                                     2.f * kapf * ((float)aF + (float)c.I.Dp[o] * (xf - (float)c.I.cen[i]));
-                    const float kt = (float)aA + (float)yD[o] - ((p + 1 < R) ? (float)yD[o + np] : 0.f);
+                                     2.f * kapf * ((float)aF + (float)c.I.Dp[o] * (xf - c.I.cenf[i]));
+                    const float kt = (float)aA + yDf[o] - ((p + 1 < R) ? yDf[o + np] : 0.f);
                     const float u = -tauf * (gf + kt);
                     v2[o] = make_float2(xf + u, u);
                 });
@@ -1394,7 +1448,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                 const double* yD = c.I.yD;
                 double* v = c.I.v;
                 const M kapm = (M)kap;
-                expand_pass<M, PCMAX>(c, P, c.om, c.yAm, [&](int i, int p, double aF, double aA) {
+                expand_pass<M, PCMAX>(c, P, c.om, c.yAm, [&](int i, int p, auto aF, auto aA) {
                     // gradient and K^T y in M; the state update in FP64
                     const size_t o = (size_t)p * np + i;
                     const double xv = x[o];
@@ -1469,7 +1523,9 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                         else
                             dy = fsD * zz;
                         const float d0y = (float)(c.I.yD0[orr] - yd);
-                        c.I.yDn[orr] = yd + (double)(fA * dy + fC * d0y);
+                        const double ydn = yd + (double)(fA * dy + fC * d0y);
+                        c.I.yDn[orr] = ydn;
+                        c.I.yDf[orr] = (float)ydn;
                         if (check) {
                             c.I.yDb[orr] = yd + (double)dy;
                             rloc[1] += (double)dy * (double)dy;
@@ -1534,7 +1590,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                     const double anv = c.vout[q * Lr + m + jj];
                     const double ya = c.yA[pe];
                     const double pA = ya + sA * (2.0 * abv - c.ax[pe]);
-                    const double qq = pA / sA;
+                    const double qq = pA * inv_sA;
                     const double cl_ = qq > c.ubd[jj] ? c.ubd[jj] : (qq < c.lb[jj] ? c.lb[jj] : qq);
                     const double yab = pA - sA * cl_;
                     const double yan = hlA * yab + hlB * ya + hlC * c.I.yA0[pe];
@@ -1578,6 +1634,10 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             if (!check) continue;
 
             // ---- (6) check: fixed-point residual and relative KKT at T(z), FP64 ----
+            // q = x_bar - (grad f + K^T y) needs a P x np FP64 buffer: v, except in the
+            // multi-period FP32-increment iteration, whose pair buffer must survive
+            // (it carries x in FP32): there the retired iterate buffer x+ serves
+            double* qbuf = (kIncr && PCMAX != 1) ? c.I.xn : c.I.v;
             // replicated parts (every CTA holds them): factor term of f at x_bar
             double fF = 0;
             for (int e = c.tid; e < P * k; e += kThreads) {
@@ -1616,8 +1676,8 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             {
                 const double* xb = c.I.xb;
                 const double* ydb = c.I.yDb;
-                double* qv = c.I.v;
-                expand_pass<double, PCMAX>(c, P, c.ub, c.yAb, [&](int i, int p, double aF, double aA) {
+                double* qv = qbuf;
+                expand_pass<double, PCMAX>(c, P, c.ub, c.yAb, [&](int i, int p, auto aF, auto aA) {
                     const size_t o = (size_t)p * np + i;
                     const double xv = xb[o];
                     const double dx = xv - c.I.cen[i];
@@ -1668,7 +1728,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                 double mx[1] = {0};
                 for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
                     const size_t o = (size_t)p * np + i;
-                    mx[0] = fmax(mx[0], fabs(c.I.xb[o] - c.I.v[o]));
+                    mx[0] = fmax(mx[0], fabs(c.I.xb[o] - qbuf[o]));
                 }
                 block_reduce<1, true>(mx, c.spart + p, c.wred, c.lane, c.warp);
             }
@@ -1678,12 +1738,12 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             __syncthreads();
             // stationarity residual ||x_bar - Proj(q)||  (thresholds warm-started
             // from the previous check)
-            l1_thresholds(cl, c, (const double*)c.I.v, c.theta, c.thq);
+            l1_thresholds(cl, c, (const double*)qbuf, c.theta, c.thq);
             double dr[1] = {0};
             for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
                 for (int p = 0; p < P; ++p) {
                     const size_t o = (size_t)p * np + i;
-                    const double qv = c.I.v[o];
+                    const double qv = qbuf[o];
                     const double aq = fabs(qv) - c.theta[p];
                     const double pq = aq > 0 ? (qv < 0 ? -aq : aq) : 0.0;
                     const double dd = c.I.xb[o] - pq;
