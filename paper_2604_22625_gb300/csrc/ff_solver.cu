@@ -1061,6 +1061,7 @@ __device__ int l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const V* vv, d
             float hi, lo, bl, bh;   // sum pair; bracket: largest |v| <= t, smallest |v| > t
             if constexpr (std::is_same<V, double>::value) {
                 double sd = 0, l = -1.0, h = INFINITY;
+#pragma unroll 4
                 for (int i = istart; i < c.i1; i += istep) {
                     const double a = fabs(vp[i]);
                     if (a > t) { sd += a; nd += 1; h = fmin(h, a); }
@@ -1083,6 +1084,7 @@ __device__ int l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const V* vv, d
                 lo = 0.f;
                 bl = -1.f;
                 bh = INFINITY;
+#pragma unroll 4
                 for (int i = istart; i < c.i1; i += istep) {
                     const float a = fabsf(vp[i].x);
                     if (a > tf) {
@@ -1136,8 +1138,9 @@ __device__ int l1_thresholds(cg::cluster_group& cl, Ctx<M, S>& c, const V* vv, d
             c.spart[2 * P + 2 * p + 1] = -bh;
         }
         team_reduce_mixed(cl, c.spart, c.sout, 4 * P, 2 * P, c.G, c.g);
-        if (c.tid == 0) {
-            for (int p = 0; p < P; ++p) {
+        // one thread per period decides (every CTA of the team holds the same sums)
+        {
+            for (int p = c.tid; p < P; p += kThreads) {
                 if (done_s[p]) continue;
                 const double Sv = c.sout[2 * p];
                 const int Nv = (int)c.sout[2 * p + 1];
