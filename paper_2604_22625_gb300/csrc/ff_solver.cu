@@ -15,9 +15,14 @@
 // Steps: tau = 2 s / L_f and sum_i sigma_i ||K_i||^2 = 1/tau - beta L_f with
 // beta > 1/2, reflection rho <= (2 beta - 1) / (2 beta).
 //
-// Precision: panels F, A stored as S and multiplied in M (FP32 or FP64) with
-// FP64 accumulation across asset chunks; the iterate state, the threshold
-// search, every elementwise update and the KKT evaluation are FP64.
+// Precision: panels F, A stored as S and multiplied in M (FP32 or FP64),
+// tile sums added in FP64.  The iterate state (x, x0, y, y0) is FP64.  In the
+// FP32/BF16 modes (M = float) each iteration's changes are computed as FP32
+// increments of FP64 differences (the step u = -tau (grad f + K^T y), the
+// projection x_bar - x, the Halpern combination, the trade residuals and the
+// dual update) and applied to the FP64 state; the l1 threshold search compares
+// in FP32 and sums as double-float pairs.  The FP64 mode keeps every operation
+// in FP64.  The KKT evaluation is FP64 in all modes.
 //
 // Work split inside a team: CTA g owns the assets [i0, i1).  Two passes over
 // the panels per iteration:
