@@ -53,6 +53,8 @@ def parse_args(argv=None):
                     choices=["batch", "single_large", "multi", "single_small", "batch_profile", "multi_profile",
                              "diff"])
     ap.add_argument("--max-iter", type=int, default=0, help="iteration cap (profiling runs only)")
+    ap.add_argument("--tuned", action="store_true", help="take cta_work / check_every from the autotuner "
+                    "(paper_2604_22625_gb300.tune; times candidates on a sample once, then cached)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true", help="call ff_solve_batch directly instead of "
                     "replaying the captured CUDA graph")
@@ -305,6 +307,12 @@ def run_ours(args):
     diff = args.workload == "diff"
     if diff:
         opt_kw["tol"] = 1e-7
+    tuned = None
+    if args.tuned:
+        from paper_2604_22625_gb300 import tune
+        tuned = tune.tune(probs, precision=precision, tol=opt_kw.get("tol", TOL),
+                          device=torch.cuda.get_device_name(dev))
+        opt_kw.update(tuned.options())
     runner = api.BatchRunner(probs, precision=precision, device=str(dev), duals=diff, **opt_kw)
     tol_ok = 1e-7 if diff else TOL
     if diff:
@@ -430,6 +438,7 @@ def run_ours(args):
                              f"{runner.ws_bytes / 2**20:.0f} MiB workspace vs {l2_mb:.0f} MiB L2)",
                        "parallelism": f"replicas x{ws} (one batch per GPU)" if ws > 1 else "1 GPU",
                        "max_iter_cap": args.max_iter or None,
+                       "schedule": tuned.options() if tuned is not None else "default (cta_work 8192, check_every 64)",
                        "graph": use_graph},
             "solved": solved, "max_rel_kkt": kkt_max,
             "iterations_mean": float(statistics.mean(iters)),

@@ -5,4 +5,4 @@ The compute path is the CUDA library ``libflashfolio.so`` (C ABI in
 calls it.  Importing the package does not load the library; ``api`` and
 ``_lib`` load it on first use and raise if it is missing.
 """
-__all__ = ["api", "synthetic", "build"]
+__all__ = ["api", "autograd", "build", "replicas", "synthetic", "tune"]
