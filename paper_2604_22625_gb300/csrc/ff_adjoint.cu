@@ -24,7 +24,6 @@
 #include <string.h>
 
 #include <algorithm>
-#include <mutex>
 #include <vector>
 
 #include "ff_internal.cuh"
@@ -77,9 +76,9 @@ __device__ double block_sum(double v, double* red) {
     return t;
 }
 
-// In-place Cholesky A = L L^T of the leading N x N block (leading dimension
-// ld, row-major, lower triangle used); returns false when a pivot is not
-// positive.  Right-looking, all threads of the CTA share the trailing update.
+// In-place Cholesky A = L L^T of the leading N x N block (row-major with
+// leading dimension lda, lower triangle used); returns false when a pivot is
+// not positive.  Right-looking, all threads of the CTA share the trailing update.
 __device__ bool cholesky(double* A, int N, int lda, double* flag) {
     for (int j = 0; j < N; ++j) {
         if (threadIdx.x == 0) {

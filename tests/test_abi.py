@@ -80,3 +80,43 @@ def test_batch_plan_groups_by_cluster_size(lib):
     o.cluster_size = 4
     cl, nl = _lib.ff_batch_plan(st, len(probs), o)
     assert set(cl) == {4} and nl == 2          # one launch per kind: single- and multi-period
+
+
+def _placeholder_problem(T=0, n=100, k=10, m=10):
+    p = _lib.ff_problem()
+    p.n, p.k, p.m, p.T, p.dtype, p.omega_diag = n, k, m, T, _lib.FF_F32, 1
+    for nm in ("F", "Omega", "D", "alpha", "s", "q", "w0", "A", "L", "U", "wT"):
+        setattr(p, nm, 1024)    # non-null placeholders: host-side checks only
+    p.GMV, p.lambda1, p.lambda2, p.lambda3, p.d = 1e9, 1e-8, 1.0, 1.0, 1.5
+    return p
+
+
+def test_invalid_options_are_rejected_on_host(lib):
+    p = _placeholder_problem()
+    ok = _lib.default_options()
+    assert _lib.ff_workspace_size(C.byref(p), 1, ok) > 0
+    for field, value in (("reflection", 0.9), ("cta_work", 0.5), ("restart_artificial", 1.0),
+                         ("reuse_workspace", 3), ("cluster_size", 3), ("tol", 0.0), ("check_every", 0)):
+        o = _lib.default_options()
+        setattr(o, field, value)
+        assert _lib.ff_workspace_size(C.byref(p), 1, o) == 0, field
+        assert _lib.ff_solve_single(p, o, 0, 0, 0, 0) == _lib.FF_ERR_INVALID_ARG, field
+
+
+def test_backward_host_checks(lib):
+    single = _placeholder_problem()
+    multi = _placeholder_problem(T=5)
+    assert _lib.ff_backward_workspace_size(single) > 0
+    assert _lib.ff_backward_workspace_size(multi) == 0
+    g = _lib.ff_grads()
+    rc = _lib.ff_backward_single(multi, 4096, 4096, 4096, 4096, g, 0, 0)
+    assert rc == _lib.FF_ERR_INVALID_ARG
+    rc = _lib.ff_backward_single(single, 4096, 4096, 4096, 4096, g, 0, 0)   # no workspace
+    assert rc == _lib.FF_ERR_WORKSPACE
+
+
+def test_batch_count_limit(lib):
+    probs = (_lib.ff_problem * 1)(_placeholder_problem())
+    o = _lib.default_options()
+    rc = _lib.ff_solve_batch(probs, 70000, o, 0, 0, 4096, [4096] * 70000)
+    assert rc == _lib.FF_ERR_UNSUPPORTED
