@@ -152,17 +152,19 @@ def _golden(fun, lo, hi, iters=300):
     return 0.5 * (a + b)
 
 
-@pytest.mark.parametrize("tight", [False, True])
-def test_separable_single(tight):
+@pytest.mark.parametrize("tight,dexp", [(False, 1.5), (True, 1.5), (False, 2.0), (True, 2.0), (False, 1.3)])
+def test_separable_single(tight, dexp):
     """F = 0 and no rows: each asset solves
     min_w -alpha w + kappa D w^2 + c1 |w - w0| + c2 |w - w0|^d + mu |w|,
-    with mu = 0 (slack budget) or mu found by bisection so that ||w||_1 = 1."""
+    with mu = 0 (slack budget) or mu found by bisection so that ||w||_1 = 1,
+    for the paper's d = 1.5, the quadratic-impact end d = 2 and an exponent
+    without a closed-form prox (d = 1.3)."""
     rng = np.random.default_rng(2)
     n = 40
     p = S.Problem(F=np.zeros((n, 1)), Omega=np.eye(1) * 1e-5, D=rng.uniform(1e-4, 9e-4, n),
                   alpha=rng.normal(0, 1e-4 if not tight else 4e-2, n), s=rng.uniform(2e-4, 2e-3, n),
                   q=rng.uniform(1e-3, 1e-2, n), w0=S._signed_l1(rng, n, 0.9 if tight else 0.5),
-                  A=np.zeros((0, n)), L=np.zeros(0), U=np.zeros(0))
+                  A=np.zeros((0, n)), L=np.zeros(0), U=np.zeros(0), d=dexp)
     sc = Scaled(p)
     kap, c1, c2, d = sc.kappa, sc.c1[0], sc.c2[0], sc.d
 
