@@ -65,9 +65,10 @@ extern "C" {
 #define FF_F32                 1
 
 /* precision modes of the solver */
-#define FF_PREC_F64            0   /* iterates, panels and reductions in FP64 */
-#define FF_PREC_F32            1   /* FP32 iterates and panels, FP64 reductions */
-#define FF_PREC_BF16           2   /* BF16 F and A panels, FP32 iterates, FP64 reductions */
+#define FF_PREC_F64            0   /* panels, products, iterates and reductions in FP64 */
+#define FF_PREC_F32            1   /* FP32 panels and products; FP64 iterate state updated by
+                                      FP32 increments; FP64 reductions and KKT */
+#define FF_PREC_BF16           2   /* BF16 F and A panels, FP32 products; otherwise as FP32 */
 
 /* One problem instance in the paper's notation and units (Eqs. 1-6).
  * Single period: T = 0; D, alpha, s, q hold n entries.
@@ -124,9 +125,12 @@ typedef struct ff_options {
                                    graph once a mode-0 call has run outside the capture). */
     double  cta_work;           /* batch scheduling: asset-periods per CTA that decide each
                                    instance's cluster size (smallest power of two G <= 16 with
-                                   n * P / G <= cta_work); default 8192.  Instances of equal G
-                                   form one persistent launch; the launches run concurrently
-                                   on library-owned streams forked from `stream`. */
+                                   n * P / G <= cta_work; while the batch would fill fewer than
+                                   half the SMs, the instance with the most work per CTA is
+                                   split further); default 8192.  Instances of equal G and kind
+                                   (single- or multi-period) form one persistent launch; the
+                                   launches run concurrently on library-owned streams forked
+                                   from `stream`. */
     double  restart_artificial; /* also restart once the iterations since the last restart
                                    reach this share of all iterations so far (0 = off);
                                    default 0.36 */
@@ -138,7 +142,10 @@ typedef struct ff_result {
     int32_t restarts;
     int64_t iterations;
     double  rel_kkt;            /* max(r_primal, r_dual, r_gap) at the returned point */
-    double  r_primal, r_dual, r_gap;
+    double  r_primal, r_dual, r_gap;   /* r_primal = ||Ax - clip(Ax)|| / (||Ax|| + ||clip(Ax)||);
+                                   r_dual = ||x - Proj(x - grad f - K^T y)|| /
+                                   (||x|| + ||grad f|| + ||K^T y||); r_gap = |P - D| /
+                                   max(|P| + |D|, Phi), Phi = sum |alpha_i x_i| + risk + cost */
     double  primal_obj;         /* scaled minimisation objective P(x) = -(Eq. 1)/GMV (+ constant, multi) */
     double  dual_obj;           /* the matching dual bound */
     double  paper_obj;          /* Eq. 1 / Eq. 4 in the paper's units (maximised) */
