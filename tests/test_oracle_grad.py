@@ -6,8 +6,9 @@ theta +- h delta (h = 1e-5, FP64; the rounding of the perturbed solves rules
 out much smaller steps): an independent route to the same number through the
 optimality conditions of the perturbed problems, not through the
 linearisation.  Cases: dead trades with active exposure rows (single period),
-an active budget with zero holdings (single period), and a multi-period
-trajectory whose dead trades tie periods together.
+an active budget with zero holdings (single period), a multi-period
+trajectory whose dead trades tie periods together, quadratic impact (d = 2)
+and a full factor covariance.
 """
 from dataclasses import replace
 
@@ -24,10 +25,21 @@ def _budget_case():
     return p
 
 
+def _full_omega_case():
+    p = S.make_single(40, 5, 41, n_onehot=1)
+    rng = np.random.default_rng(41)
+    Q, _ = np.linalg.qr(rng.standard_normal((5, 5)))
+    p.Omega = Q @ np.diag(rng.uniform(1e-5, 1e-4, 5)) @ Q.T
+    p.Omega = 0.5 * (p.Omega + p.Omega.T)
+    return p
+
+
 CASES = {
     "single_dead_rows": lambda: S.make_single(40, 6, 11, n_onehot=2),
     "single_budget_zeros": _budget_case,
     "multi_T4": lambda: S.make_multi(4, 20, 4, 12, n_onehot=2),
+    "single_quadratic_impact": lambda: S.make_single(40, 6, 17, n_onehot=2, d=2.0),
+    "single_full_omega": _full_omega_case,
 }
 
 
@@ -39,7 +51,7 @@ def test_jvp_matches_central_differences_of_solves(case):
     red = sol.reduced
     if case == "single_budget_zeros":
         assert red.budget[0] and int((red.sx == 0).sum()) > 0
-    else:
+    elif case in ("single_dead_rows", "multi_T4"):
         assert int((~red.live).sum()) > 0 and len(red.box) > 0
     rng = np.random.default_rng(7)
     h = 1e-5
