@@ -273,6 +273,16 @@ size_t ff_backward_workspace_size(const ff_problem* p);
 int ff_backward_single(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,
                        const ff_grads* out, void* ws, size_t ws_bytes, int32_t* status_dev, void* stream);
 
+/* The adjoint entry point for any instance (the differentiable layer of
+ * Sec. 2, implicit differentiation of the solve): same arguments, layout,
+ * ownership and results as ff_backward_single.  A single-period instance
+ * (p->T == 0, Eqs. 1-3) is differentiated exactly as there; a multi-period
+ * instance (p->T >= 2, Eqs. 4-6) returns FF_ERR_UNSUPPORTED without touching
+ * any buffer (its adjoint is not built); an invalid p returns
+ * FF_ERR_INVALID_ARG.  Host-side checks only; asynchronous on `stream`. */
+int ff_backward(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,
+                const ff_grads* out, void* ws, size_t ws_bytes, int32_t* status_dev, void* stream);
+
 /* ff_backward_single for `count` single-period instances in one launch (one
  * CTA per instance).  probs, w, yA, yD, grad_w and out are HOST arrays of
  * count entries (pointers inside are DEVICE pointers as in

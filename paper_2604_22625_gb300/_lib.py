@@ -80,7 +80,7 @@ assert RESULT_DTYPE.itemsize == C.sizeof(ff_result)
 
 EXPORTS = ("ff_default_options", "ff_workspace_size", "ff_solve_single", "ff_solve_multi",
            "ff_solve_batch", "ff_status_string", "ff_version", "ff_last_error",
-           "ff_solve_single_static", "ff_batch_plan", "ff_backward_single", "ff_backward_workspace_size",
+           "ff_solve_single_static", "ff_batch_plan", "ff_backward", "ff_backward_single", "ff_backward_workspace_size",
            "ff_backward_batch", "ff_backward_batch_workspace_size")
 
 _lib = None
@@ -108,6 +108,8 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.ff_backward_single.argtypes = [C.POINTER(ff_problem), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.POINTER(ff_grads), C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]
     lib.ff_backward_single.restype = C.c_int
+    lib.ff_backward.argtypes = lib.ff_backward_single.argtypes
+    lib.ff_backward.restype = C.c_int
     lib.ff_backward_batch_workspace_size.argtypes = [C.POINTER(ff_problem), C.c_int]
     lib.ff_backward_batch_workspace_size.restype = C.c_size_t
     vp = C.POINTER(C.c_void_p)
@@ -176,6 +178,13 @@ def ff_backward_single(prob: ff_problem, w: int, yA: int, yD: int, grad_w: int, 
     return int(load().ff_backward_single(C.byref(prob), C.c_void_p(w), C.c_void_p(yA or None), C.c_void_p(yD),
                                          C.c_void_p(grad_w), C.byref(grads), C.c_void_p(ws), ws_bytes,
                                          C.c_void_p(status or None), C.c_void_p(stream or None)))
+
+
+def ff_backward(prob: ff_problem, w: int, yA: int, yD: int, grad_w: int, grads: ff_grads, ws: int,
+                ws_bytes: int, status: int = 0, stream: int = 0) -> int:
+    return int(load().ff_backward(C.byref(prob), C.c_void_p(w), C.c_void_p(yA or None), C.c_void_p(yD),
+                                  C.c_void_p(grad_w), C.byref(grads), C.c_void_p(ws), ws_bytes,
+                                  C.c_void_p(status or None), C.c_void_p(stream or None)))
 
 
 def ff_batch_plan(probs, count: int, opts: ff_options):

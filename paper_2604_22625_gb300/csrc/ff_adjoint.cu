@@ -415,6 +415,9 @@ AdjInst carve_adj(const ff_problem* p, const void* w, const void* yA, const void
 
 extern "C" {
 
+int ff_backward_single(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,
+                       const ff_grads* out, void* ws, size_t ws_bytes, int32_t* status_dev, void* stream);
+
 size_t ff_backward_workspace_size(const ff_problem* p) {
     if (!p || p->T != 0 || p->n < 1 || p->k < 1 || p->m < 0) return 0;
     return ff::a256(sizeof(ff::AdjInst)) + ff::adj_bytes(p->n, p->k, p->m);
@@ -454,6 +457,12 @@ int ff_backward_batch(const ff_problem* probs, int count, const void* const* w, 
     e = cudaGetLastError();
     if (e != cudaSuccess) return FF_ERR_CUDA;
     return FF_OK;
+}
+
+int ff_backward(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,
+                const ff_grads* out, void* ws, size_t ws_bytes, int32_t* status_dev, void* stream) {
+    if (p && p->T >= 2) return FF_ERR_UNSUPPORTED;   // the multi-period adjoint is not built
+    return ff_backward_single(p, w, yA, yD, grad_w, out, ws, ws_bytes, status_dev, stream);
 }
 
 int ff_backward_single(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,

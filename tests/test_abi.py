@@ -113,6 +113,9 @@ def test_backward_host_checks(lib):
     assert rc == _lib.FF_ERR_INVALID_ARG
     rc = _lib.ff_backward_single(single, 4096, 4096, 4096, 4096, g, 0, 0)   # no workspace
     assert rc == _lib.FF_ERR_WORKSPACE
+    # the general entry point: same checks for a single period, unsupported for T >= 2
+    assert _lib.ff_backward(single, 4096, 4096, 4096, 4096, g, 0, 0) == _lib.FF_ERR_WORKSPACE
+    assert _lib.ff_backward(multi, 4096, 4096, 4096, 4096, g, 0, 0) == _lib.FF_ERR_UNSUPPORTED
 
 
 def test_batch_count_limit(lib):
