@@ -15,8 +15,8 @@ implicit function theorem then gives the directional derivative
 with H the Hessian of the reduced objective, the dense KKT matrix solved by
 LAPACK.  The t-derivatives of r, e and x_fix at fixed v are taken by central
 differences of those functions themselves (they are polynomial in alpha, F,
-D, s, q, so the differences are exact up to rounding; smooth in w0 on live
-trades): no hand-derived partial derivative enters, so this oracle is
+D, s, q, so the differences are exact up to rounding; smooth in w0 and w_T on
+live trades): no hand-derived partial derivative enters, so this oracle is
 independent of the adjoint formulas of the CUDA path.
 """
 from __future__ import annotations
@@ -29,6 +29,7 @@ from .active import hessian_grad
 from .model import Scaled
 
 PARAMS = ("alpha", "F", "D", "s", "q", "w0")
+MULTI_PARAMS = PARAMS + ("wT",)   # the fixed final portfolio of Eq. 4 (multi-period only)
 
 
 def _fixed_sources(sc: Scaled, red):
@@ -65,9 +66,10 @@ def _rhs_e(sc: Scaled, red, x_fix):
 
 def jvp(prob, sol, name: str, delta, h: float = None) -> np.ndarray:
     """dx*/dtheta applied to the direction ``delta`` of parameter ``name``
-    (one of alpha, F, D, s, q, w0), shape (P, n).  ``sol`` is a polished
-    ``oracle.solve`` result (it carries the reduced problem)."""
-    if name not in PARAMS:
+    (one of alpha, F, D, s, q, w0, and wT for a multi-period problem),
+    shape (P, n).  ``sol`` is a polished ``oracle.solve`` result (it carries
+    the reduced problem)."""
+    if name not in (MULTI_PARAMS if int(getattr(prob, "T", 0)) >= 2 else PARAMS):
         raise ValueError(name)
     red = sol.reduced
     if red is None:
@@ -82,7 +84,7 @@ def jvp(prob, sol, name: str, delta, h: float = None) -> np.ndarray:
     delta = np.asarray(delta, dtype=np.float64).reshape(base.shape)
     if h is None:
         scale = max(float(np.max(np.abs(base))), 1e-12) / max(float(np.max(np.abs(delta))), 1e-300)
-        if name == "w0":
+        if name in ("w0", "wT"):
             z = sc.trades(x)
             live = np.abs(z[red.live]) if np.any(red.live) else np.array([1.0])
             h = 1e-4 * float(np.min(live)) / max(float(np.max(np.abs(delta))), 1e-300)

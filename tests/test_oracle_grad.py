@@ -7,8 +7,9 @@ out much smaller steps): an independent route to the same number through the
 optimality conditions of the perturbed problems, not through the
 linearisation.  Cases: dead trades with active exposure rows (single period),
 an active budget with zero holdings (single period), a multi-period
-trajectory whose dead trades tie periods together, quadratic impact (d = 2)
-and a full factor covariance.
+trajectory whose dead trades tie periods together (also differentiated in
+the fixed final portfolio w_T), quadratic impact (d = 2) and a full factor
+covariance.
 """
 from dataclasses import replace
 
@@ -55,7 +56,8 @@ def test_jvp_matches_central_differences_of_solves(case):
         assert int((~red.live).sum()) > 0 and len(red.box) > 0
     rng = np.random.default_rng(7)
     h = 1e-5
-    for name in OG.PARAMS:
+    names = OG.MULTI_PARAMS if case.startswith("multi") else OG.PARAMS
+    for name in names:
         base = np.asarray(getattr(prob, name))
         delta = rng.standard_normal(base.shape) * np.abs(base).mean()
         dx = OG.jvp(prob, sol, name, delta)
