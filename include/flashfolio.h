@@ -235,9 +235,11 @@ int ff_batch_plan(const ff_problem* probs, int count, const ff_options* o, int32
 /* Message for an FF_* return code (static storage). */
 const char* ff_status_string(int code);
 
-/* Gradient outputs of ff_backward_single: DEVICE pointers with the layout and
- * element type of the matching ff_problem arrays (alpha, D, s, q, w0: n
- * entries; F: n x k row-major).  Any may be NULL (not computed). */
+/* Gradient outputs of the adjoint calls: DEVICE pointers with the layout and
+ * element type of the matching ff_problem arrays (single period: alpha, D, s,
+ * q, w0 hold n entries; multi-period: alpha, D, s, q hold T x n and w0, wT n;
+ * F: n x k row-major).  Any may be NULL (not computed).  wT is used by
+ * multi-period instances only. */
 typedef struct ff_grads {
     void* alpha;
     void* F;
@@ -245,10 +247,12 @@ typedef struct ff_grads {
     void* s;
     void* q;
     void* w0;
+    void* wT;
 } ff_grads;
 
-/* Workspace bytes of ff_backward_single for this problem (host only; 0 if p
- * is invalid or multi-period). */
+/* Workspace bytes of ff_backward for this problem (host only; 0 if p is
+ * invalid): the single-period adjoint for T == 0, the multi-period one
+ * (ff_backward_multi_workspace_size of this one instance) for T >= 2. */
 size_t ff_backward_workspace_size(const ff_problem* p);
 
 /* Vector-Jacobian product of the single-period solve (Sec. 2.1, Eqs. 1-3):
@@ -273,15 +277,48 @@ size_t ff_backward_workspace_size(const ff_problem* p);
 int ff_backward_single(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,
                        const ff_grads* out, void* ws, size_t ws_bytes, int32_t* status_dev, void* stream);
 
-/* The adjoint entry point for any instance (the differentiable layer of
- * Sec. 2, implicit differentiation of the solve): same arguments, layout,
- * ownership and results as ff_backward_single.  A single-period instance
- * (p->T == 0, Eqs. 1-3) is differentiated exactly as there; a multi-period
- * instance (p->T >= 2, Eqs. 4-6) returns FF_ERR_UNSUPPORTED without touching
- * any buffer (its adjoint is not built); an invalid p returns
- * FF_ERR_INVALID_ARG.  Host-side checks only; asynchronous on `stream`. */
+/* The adjoint entry point for any instance (implicit differentiation of the
+ * solve): a single-period instance (p->T == 0, Eqs. 1-3) goes to
+ * ff_backward_single, a multi-period one (p->T >= 2, Eqs. 4-6) to
+ * ff_backward_multi_batch with count 1; arguments, layouts, statuses and
+ * workspace as there (ff_backward_workspace_size covers both).  Invalid
+ * arguments return FF_ERR_INVALID_ARG before anything is enqueued. */
 int ff_backward(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,
                 const ff_grads* out, void* ws, size_t ws_bytes, int32_t* status_dev, void* stream);
+
+/* Workspace bytes of ff_backward_multi_batch for these instances (host only;
+ * 0 if an instance is not multi-period or a size is invalid).  Per instance it
+ * is about 333 (T-1) n + 16 ((T-1)(m+1))^2 bytes: the second term holds the
+ * matrix of the active constraint rows and its inverse. */
+size_t ff_backward_multi_workspace_size(const ff_problem* probs, int count);
+
+/* Vector-Jacobian products of the multi-period solve (Sec. 2.2, Eqs. 4-6) for
+ * `count` instances (all with T >= 2): with L = <grad_w, x*> summed over the
+ * T-1 free periods, writes dL/dalpha, dL/dD, dL/ds, dL/dq (T x n each; the
+ * rows t = T of alpha and D receive 0, they enter only a constant), dL/dF
+ * (n x k), dL/dw0 and dL/dwT (n each) to out[t] (paper units, as passed).
+ * The active structure is read from the forward results of ff_solve_multi /
+ * ff_solve_batch: dead trades |yD_{r,i}| < lambda2 s_{r,i} (they tie
+ * neighbouring periods, or a period to w0 / w_T), zero holdings w == 0, the
+ * budget of period t when ||w_t||_1 >= 1 - 1e-10 (FP64 data; 1 - 1e-6 for
+ * FP32), exposure rows with |yA| > 1e-12 max|yA|.  The reduced KKT system is
+ * solved in FP64 on the GPU by projected conjugate gradients (per-asset
+ * tridiagonal preconditioner; constraint rows through the explicit inverse of
+ * E M^-1 E^T, with linearly dependent rows dropped); A is treated as
+ * independent data (no derivative through A).
+ *   probs, w, yA, yD, grad_w, out : HOST arrays of count entries; the pointers
+ *       inside are DEVICE pointers: w (T-1) x n, yA (T-1) x m (NULL allowed when
+ *       m = 0), yD T x n, grad_w (T-1) x n, all of the problem's dtype.
+ *   status_dev : device array of count int32 or NULL: 0 ok, 3 the conjugate
+ *       gradients reached their iteration limit (600), 4 a non-positive or
+ *       non-finite curvature / residual was met (degenerate active set).
+ *   ws : device workspace of ff_backward_multi_workspace_size bytes, 256-byte
+ *       aligned; its contents are overwritten.
+ * Asynchronous on `stream` (about 6,000 kernel launches; no host
+ * synchronisation); FF_OK or an FF_ERR_* code. */
+int ff_backward_multi_batch(const ff_problem* probs, int count, const void* const* w, const void* const* yA,
+                            const void* const* yD, const void* const* grad_w, const ff_grads* out, void* ws,
+                            size_t ws_bytes, int32_t* status_dev, void* stream);
 
 /* ff_backward_single for `count` single-period instances in one launch (one
  * CTA per instance).  probs, w, yA, yD, grad_w and out are HOST arrays of

@@ -61,7 +61,7 @@ class ff_options(C.Structure):
 
 class ff_grads(C.Structure):
     _fields_ = [("alpha", C.c_void_p), ("F", C.c_void_p), ("D", C.c_void_p), ("s", C.c_void_p),
-                ("q", C.c_void_p), ("w0", C.c_void_p)]
+                ("q", C.c_void_p), ("w0", C.c_void_p), ("wT", C.c_void_p)]
 
 
 class ff_result(C.Structure):
@@ -81,7 +81,8 @@ assert RESULT_DTYPE.itemsize == C.sizeof(ff_result)
 EXPORTS = ("ff_default_options", "ff_workspace_size", "ff_solve_single", "ff_solve_multi",
            "ff_solve_batch", "ff_status_string", "ff_version", "ff_last_error",
            "ff_solve_single_static", "ff_batch_plan", "ff_backward", "ff_backward_single", "ff_backward_workspace_size",
-           "ff_backward_batch", "ff_backward_batch_workspace_size")
+           "ff_backward_batch", "ff_backward_batch_workspace_size", "ff_backward_multi_batch",
+           "ff_backward_multi_workspace_size")
 
 _lib = None
 
@@ -116,6 +117,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.ff_backward_batch.argtypes = [C.POINTER(ff_problem), C.c_int, vp, vp, vp, vp, C.POINTER(ff_grads),
                                       C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]
     lib.ff_backward_batch.restype = C.c_int
+    lib.ff_backward_multi_workspace_size.argtypes = [C.POINTER(ff_problem), C.c_int]
+    lib.ff_backward_multi_workspace_size.restype = C.c_size_t
+    lib.ff_backward_multi_batch.argtypes = lib.ff_backward_batch.argtypes
+    lib.ff_backward_multi_batch.restype = C.c_int
     lib.ff_batch_plan.argtypes = [C.POINTER(ff_problem), C.c_int, C.POINTER(ff_options),
                                   C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.ff_batch_plan.restype = C.c_int
@@ -218,6 +223,20 @@ def ff_backward_batch(probs, count: int, w_ptrs, yA_ptrs, yD_ptrs, g_ptrs, grads
     return int(load().ff_backward_batch(probs, count, arr(w_ptrs), arr(yA_ptrs), arr(yD_ptrs), arr(g_ptrs), gr,
                                         C.c_void_p(ws), ws_bytes, C.c_void_p(status or None),
                                         C.c_void_p(stream or None)))
+
+
+def ff_backward_multi_workspace_size(probs, count: int) -> int:
+    return int(load().ff_backward_multi_workspace_size(probs, count))
+
+
+def ff_backward_multi_batch(probs, count: int, w_ptrs, yA_ptrs, yD_ptrs, g_ptrs, grads, ws: int, ws_bytes: int,
+                            status: int = 0, stream: int = 0) -> int:
+    def arr(v):
+        return (C.c_void_p * count)(*v) if v is not None else None
+    gr = (ff_grads * count)(*grads)
+    return int(load().ff_backward_multi_batch(probs, count, arr(w_ptrs), arr(yA_ptrs), arr(yD_ptrs), arr(g_ptrs),
+                                              gr, C.c_void_p(ws), ws_bytes, C.c_void_p(status or None),
+                                              C.c_void_p(stream or None)))
 
 
 def ff_status_string(code: int) -> str:

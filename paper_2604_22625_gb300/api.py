@@ -295,14 +295,14 @@ class BatchRunner:
             self.res_host.copy_(self.res, non_blocking=True)
 
     def prepare_backward(self) -> None:
-        """Buffers of the batched adjoint (single-period instances, duals on):
-        ``g_dev`` holds the upstream gradients in the portfolio layout,
-        ``grad_dev`` the gradients of alpha, F, D, s, q, w0 in the packed
-        input layout (``layout``)."""
+        """Buffers of the batched adjoint (duals on): ``g_dev`` holds the
+        upstream gradients in the portfolio layout, ``grad_dev`` the gradients
+        of alpha, F, D, s, q, w0 (and w_T for multi-period instances) in the
+        packed input layout (``layout``).  Single-period instances go to
+        ``ff_backward_batch``, multi-period ones to ``ff_backward_multi_batch``;
+        ``bstatus`` holds every instance's adjoint status (instance order)."""
         if self.yD_ptrs is None:
             raise ValueError("BatchRunner(duals=True) is needed for the adjoint")
-        if any(int(p.T) >= 2 for p in self.problems):
-            raise ValueError("the adjoint covers single-period instances")
         self.g_dev = torch.zeros_like(self.w_dev)
         self.grad_dev = torch.zeros_like(self.dev_in)
         elem = self.grad_dev.element_size()
@@ -312,21 +312,43 @@ class BatchRunner:
         self.grads = []
         for ent in self.layout:
             gr = L.ff_grads()
-            for nm in ("alpha", "F", "D", "s", "q", "w0"):
-                setattr(gr, nm, base + ent[nm][0] * elem)
+            for nm in ("alpha", "F", "D", "s", "q", "w0", "wT"):
+                setattr(gr, nm, base + ent[nm][0] * elem if nm in ent else None)
             self.grads.append(gr)
-        self.bws_bytes = L.ff_backward_batch_workspace_size(self.structs, self.count)
-        self.bws = torch.empty(self.bws_bytes, dtype=torch.uint8, device=self.device)
-        self.bstatus = torch.zeros(self.count, dtype=torch.int32, device=self.device)
+        single = [i for i, p in enumerate(self.problems) if int(p.T) < 2]
+        multi = [i for i, p in enumerate(self.problems) if int(p.T) >= 2]
+        self._bstatus_sub = torch.zeros(self.count, dtype=torch.int32, device=self.device)
+        self._border = single + multi
+        self._bsets = []
+        pos = 0
+        for idx, size_fn, call in ((single, L.ff_backward_batch_workspace_size, L.ff_backward_batch),
+                                   (multi, L.ff_backward_multi_workspace_size, L.ff_backward_multi_batch)):
+            if not idx:
+                continue
+            structs = (L.ff_problem * len(idx))(*[self.structs[i] for i in idx])
+            nb = size_fn(structs, len(idx))
+            if nb == 0:
+                raise ValueError("invalid problem for the adjoint")
+            ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+            self._bsets.append((idx, structs, ws, nb, call, self._bstatus_sub.data_ptr() + 4 * pos))
+            pos += len(idx)
+
+    @property
+    def bstatus(self) -> torch.Tensor:
+        """Adjoint status of every instance, in instance order."""
+        out = torch.empty_like(self._bstatus_sub)
+        out[torch.tensor(self._border, device=self.device)] = self._bstatus_sub
+        return out
 
     def backward(self, stream: Optional[torch.cuda.Stream] = None) -> None:
         """Vector-Jacobian products of every instance for the gradients in g_dev."""
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
-        rc = L.ff_backward_batch(self.structs, self.count, self.w_ptrs, self.yA_ptrs, self.yD_ptrs, self.g_ptrs,
-                                 self.grads, self.bws.data_ptr(), self.bws_bytes, self.bstatus.data_ptr(),
-                                 s.cuda_stream)
-        if rc != L.FF_OK:
-            raise RuntimeError(f"backward failed: {L.ff_status_string(rc)} ({rc}) {L.ff_last_error()}")
+        for idx, structs, ws, nb, call, status in self._bsets:
+            pick = lambda v: [v[i] for i in idx]   # noqa: E731
+            rc = call(structs, len(idx), pick(self.w_ptrs), pick(self.yA_ptrs), pick(self.yD_ptrs),
+                      pick(self.g_ptrs), pick(self.grads), ws.data_ptr(), nb, status, s.cuda_stream)
+            if rc != L.FF_OK:
+                raise RuntimeError(f"backward failed: {L.ff_status_string(rc)} ({rc}) {L.ff_last_error()}")
 
     def gradient(self, i: int, name: str) -> np.ndarray:
         off, size = self.layout[i][name]

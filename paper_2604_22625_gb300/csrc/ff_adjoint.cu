@@ -419,6 +419,7 @@ int ff_backward_single(const ff_problem* p, const void* w, const void* yA, const
                        const ff_grads* out, void* ws, size_t ws_bytes, int32_t* status_dev, void* stream);
 
 size_t ff_backward_workspace_size(const ff_problem* p) {
+    if (p && p->T >= 2) return ff_backward_multi_workspace_size(p, 1);
     if (!p || p->T != 0 || p->n < 1 || p->k < 1 || p->m < 0) return 0;
     return ff::a256(sizeof(ff::AdjInst)) + ff::adj_bytes(p->n, p->k, p->m);
 }
@@ -461,7 +462,13 @@ int ff_backward_batch(const ff_problem* probs, int count, const void* const* w, 
 
 int ff_backward(const ff_problem* p, const void* w, const void* yA, const void* yD, const void* grad_w,
                 const ff_grads* out, void* ws, size_t ws_bytes, int32_t* status_dev, void* stream) {
-    if (p && p->T >= 2) return FF_ERR_UNSUPPORTED;   // the multi-period adjoint is not built
+    if (p && p->T >= 2) {
+        const void* wv[1] = {w};
+        const void* ya[1] = {yA};
+        const void* yd[1] = {yD};
+        const void* gv[1] = {grad_w};
+        return ff_backward_multi_batch(p, 1, wv, ya, yd, gv, out, ws, ws_bytes, status_dev, stream);
+    }
     return ff_backward_single(p, w, yA, yD, grad_w, out, ws, ws_bytes, status_dev, stream);
 }
 

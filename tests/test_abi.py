@@ -107,15 +107,46 @@ def test_backward_host_checks(lib):
     single = _placeholder_problem()
     multi = _placeholder_problem(T=5)
     assert _lib.ff_backward_workspace_size(single) > 0
-    assert _lib.ff_backward_workspace_size(multi) == 0
     g = _lib.ff_grads()
     rc = _lib.ff_backward_single(multi, 4096, 4096, 4096, 4096, g, 0, 0)
     assert rc == _lib.FF_ERR_INVALID_ARG
     rc = _lib.ff_backward_single(single, 4096, 4096, 4096, 4096, g, 0, 0)   # no workspace
     assert rc == _lib.FF_ERR_WORKSPACE
-    # the general entry point: same checks for a single period, unsupported for T >= 2
+    # the general entry point routes by kind; both stop at the missing workspace
     assert _lib.ff_backward(single, 4096, 4096, 4096, 4096, g, 0, 0) == _lib.FF_ERR_WORKSPACE
-    assert _lib.ff_backward(multi, 4096, 4096, 4096, 4096, g, 0, 0) == _lib.FF_ERR_UNSUPPORTED
+    assert _lib.ff_backward(multi, 4096, 4096, 4096, 4096, g, 0, 0) == _lib.FF_ERR_WORKSPACE
+    bad = _placeholder_problem(T=5)
+    bad.wT = None                                  # w_T is required for a multi-period adjoint
+    assert _lib.ff_backward(bad, 4096, 4096, 4096, 4096, g, 0, 0) == _lib.FF_ERR_INVALID_ARG
+
+
+def test_multi_backward_host_checks(lib):
+    """Workspace sizes and argument checks of the multi-period adjoint (host only)."""
+    assert C.sizeof(_lib.ff_grads) == 7 * C.sizeof(C.c_void_p)
+    multi = _placeholder_problem(T=5)
+    one = (_lib.ff_problem * 1)(multi)
+    ws1 = _lib.ff_backward_multi_workspace_size(one, 1)
+    assert ws1 > 0 and _lib.ff_backward_workspace_size(multi) == ws1
+    two = (_lib.ff_problem * 2)(multi, _placeholder_problem(T=9, n=300))
+    assert _lib.ff_backward_multi_workspace_size(two, 2) > ws1
+    mixed = (_lib.ff_problem * 2)(multi, _placeholder_problem())
+    assert _lib.ff_backward_multi_workspace_size(mixed, 2) == 0      # single-period instance
+    # the documented estimate: about 333 (T-1) n + 16 ((T-1)(m+1))^2 bytes
+    big = (_lib.ff_problem * 1)(_placeholder_problem(T=50, n=2000, k=60, m=60))
+    est = 333 * 49 * 2000 + 16 * (49 * 61) ** 2
+    assert abs(_lib.ff_backward_multi_workspace_size(big, 1) / est - 1) < 0.02
+    g = [_lib.ff_grads()]
+    ptr = [4096]
+    rc = _lib.ff_backward_multi_batch(mixed, 2, ptr * 2, ptr * 2, ptr * 2, ptr * 2, g * 2, 0, 0)
+    assert rc == _lib.FF_ERR_INVALID_ARG
+    rc = _lib.ff_backward_multi_batch(one, 1, ptr, ptr, ptr, ptr, g, 0, 0)
+    assert rc == _lib.FF_ERR_WORKSPACE
+    rc = _lib.ff_backward_multi_batch(one, 1, ptr, ptr, ptr, ptr, g, 256 * 17, 1024)   # too small
+    assert rc == _lib.FF_ERR_WORKSPACE
+    rc = _lib.ff_backward_multi_batch(one, 1, ptr, ptr, None, ptr, g, 256 * 17, ws1)   # no yD
+    assert rc == _lib.FF_ERR_INVALID_ARG
+    rc = _lib.ff_backward_multi_batch(one, 70000, ptr, ptr, ptr, ptr, g, 256 * 17, ws1)
+    assert rc == _lib.FF_ERR_INVALID_ARG
 
 
 def test_batch_count_limit(lib):

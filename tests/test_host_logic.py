@@ -79,3 +79,54 @@ def test_algorithmic_bytes_formula():
     s = S.make_single(100, 8, 3, n_onehot=2)
     want_f64 = 2 * (n * k + m * n) * 8 + ((2 + 2 + 2) * n + 2 * m) * 8 + 3 * (n + m + n) * 8
     assert bench.algorithmic_bytes_per_iter(s, "f64") == want_f64
+
+
+def test_batchrunner_backward_dispatch(monkeypatch):
+    """BatchRunner sends single-period instances to ff_backward_batch and
+    multi-period ones to ff_backward_multi_batch, each with its own pointers,
+    gradients (w_T for multi-period only), workspace and status slots, and
+    reports the statuses in instance order (host logic; the C calls are
+    recorded, not run)."""
+    import torch
+
+    from paper_2604_22625_gb300 import _lib as L
+    from paper_2604_22625_gb300 import api
+    from paper_2604_22625_gb300.build import build
+    build()
+    probs = [S.make_single(30, 4, 1, n_onehot=2), S.make_multi(3, 20, 4, 2, n_onehot=2),
+             S.make_single(50, 4, 3, n_onehot=2), S.make_multi(4, 25, 4, 4, n_onehot=2)]
+    calls = []
+
+    def rec(kind):
+        def f(structs, count, w, yA, yD, g, grads, ws, nb, status, stream):
+            calls.append(dict(kind=kind, T=[structs[t].T for t in range(count)], count=count, w=list(w),
+                              yA=list(yA), yD=list(yD), g=list(g), wT=[gr.wT for gr in grads],
+                              alpha=[gr.alpha for gr in grads], nb=nb, status=status))
+            return L.FF_OK
+        return f
+
+    monkeypatch.setattr(L, "ff_backward_batch", rec("single"))
+    monkeypatch.setattr(L, "ff_backward_multi_batch", rec("multi"))
+    br = api.BatchRunner(probs, precision="f64", device="cpu", duals=True)
+    br.prepare_backward()
+
+    class _Stream:
+        cuda_stream = 0
+
+    br.backward(_Stream())
+    assert [c["kind"] for c in calls] == ["single", "multi"]
+    single, multi = calls
+    assert single["count"] == 2 and single["T"] == [0, 0]
+    assert multi["count"] == 2 and multi["T"] == [3, 4]
+    for c, idx in ((single, [0, 2]), (multi, [1, 3])):
+        assert c["w"] == [br.w_ptrs[i] for i in idx]
+        assert c["yA"] == [br.yA_ptrs[i] for i in idx] and c["yD"] == [br.yD_ptrs[i] for i in idx]
+        assert c["g"] == [br.g_ptrs[i] for i in idx]
+        assert c["alpha"] == [br.grads[i].alpha for i in idx]
+    assert single["wT"] == [None, None] and all(v for v in multi["wT"])
+    assert single["nb"] == L.ff_backward_batch_workspace_size(
+        (L.ff_problem * 2)(br.structs[0], br.structs[2]), 2)
+    base = br._bstatus_sub.data_ptr()
+    assert single["status"] == base and multi["status"] == base + 8
+    br._bstatus_sub.copy_(torch.tensor([10, 12, 11, 13], dtype=torch.int32))
+    assert br.bstatus.tolist() == [10, 11, 12, 13]
