@@ -61,13 +61,15 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-instance form")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the CPU baseline sample")
+    ap.add_argument("--diff-multi", type=int, default=0, help="differentiation workload: also this many "
+                    "multi-period instances (T=50, n=2000, k=60) through the multi-period adjoint")
     return ap.parse_args(argv)
 
 
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
-def make_workload(name: str, rank: int):
+def make_workload(name: str, rank: int, diff_multi: int = 0):
     """(problems, precision, description) of a named workload; rank seeds it."""
     from paper_2604_22625_gb300 import synthetic as S
     if name == "batch":
@@ -83,10 +85,12 @@ def make_workload(name: str, rank: int):
         probs = sorted([p for p in allp if int(p.T) >= 2], key=lambda p: -p.n * p.T)[:8]
         return probs, "bf16", "profiling case: the 8 largest multi-period instances of the batched workload"
     if name == "diff":
-        probs = S.config_diff(seed=rank_seed(4, rank), n_single=64, n_multi=0)
-        return probs, "f32", ("differentiation: 64 single-period instances n=3000 k=60, forward to 1e-7 "
-                              "relative KKT then the batched adjoint (vector-Jacobian products for alpha, F, D, "
-                              "s, q, w0)")
+        probs = S.config_diff(seed=rank_seed(4, rank), n_single=64, n_multi=diff_multi)
+        extra = (f" + {diff_multi} multi-period instances T=50 n=2000 k=60 (vector-Jacobian products also for "
+                 "w_T)") if diff_multi else ""
+        return probs, "f32", ("differentiation: 64 single-period instances n=3000 k=60" + extra + ", forward to "
+                              "1e-7 relative KKT then the batched adjoint (vector-Jacobian products for alpha, "
+                              "F, D, s, q, w0)")
     if name == "single_large":
         return [S.config_single_large(seed=rank_seed(1, rank))], "f32", "single-period n=10000 k=100 m=160, FP32"
     if name == "multi":
@@ -242,7 +246,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    probs, precision, desc = make_workload(args.workload, 0)
+    probs, precision, desc = make_workload(args.workload, 0, args.diff_multi)
     singles = [p for p in probs if int(p.T) < 2]
     multis = [p for p in probs if int(p.T) >= 2]
 
@@ -300,7 +304,7 @@ def run_ours(args):
     from paper_2604_22625_gb300.build import build
     build()
 
-    probs, precision, desc = make_workload(args.workload, rank)
+    probs, precision, desc = make_workload(args.workload, rank, args.diff_multi)
     opt_kw = {"time_limit": 600.0}
     if args.max_iter > 0:
         opt_kw["max_iter"] = args.max_iter
@@ -362,7 +366,7 @@ def run_ours(args):
     inst_s = [float(i["seconds"]) for i in infos]
     alg_bytes = float(sum(b * it for b, it in zip(bpi, iters)))
 
-    launches_per_step = 1 + runner.solver_launches() + (1 if diff else 0)
+    launches_per_step = 1 + runner.solver_launches() + (runner.backward_launches() if diff else 0)
     t_max = max_over_ranks(dist, dev_s, dev)
     solved_all = sum_over_ranks(dist, float(solved * args.steps), dev)
     value = solved_all / t_max if t_max > 0 else 0.0
