@@ -118,3 +118,34 @@ def test_full_size_vjp_alpha_matches_solve_differences(torch_mod):
         vals.append(float(np.sum(gs[0] * b2.portfolios()[0])))
     fd = (vals[0] - vals[1]) / (2 * h)
     assert abs(a - fd) <= 1e-2 * abs(fd), (a, fd)
+
+
+def test_autograd_multi_matches_oracle(torch_mod):
+    """solve_diff_multi: L = <g, x*> back-propagated through torch autograd
+    gives the oracle's derivative for every parameter block, w_T included."""
+    torch = torch_mod
+    from paper_2604_22625_gb300.autograd import SolveParams, solve_diff_multi
+    prob = CASES["ties_w0_wT_f64"][0]()
+    sol = oracle.solve(prob)
+    dev = "cuda"
+    t = {nm: torch.tensor(np.asarray(getattr(prob, nm), dtype=np.float64), device=dev)
+         for nm in ("alpha", "F", "D", "s", "q", "w0", "wT", "A", "L", "U")}
+    t["Omega"] = torch.tensor(np.diag(prob.Omega).copy(), device=dev)
+    for nm in OG.MULTI_PARAMS:
+        t[nm].requires_grad_(True)
+    prm = SolveParams(GMV=prob.GMV, lam1=prob.lam1, lam2=prob.lam2, lam3=prob.lam3, d=prob.d, precision="f64",
+                      tol=1e-10)
+    x = solve_diff_multi(t["alpha"], t["F"], t["D"], t["s"], t["q"], t["w0"], t["wT"], t["Omega"], t["A"],
+                         t["L"], t["U"], prm)
+    rng = np.random.default_rng(8)
+    g = rng.standard_normal(sol.x.shape)
+    (x * torch.tensor(g, device=dev)).sum().backward()
+    torch.cuda.synchronize()
+    assert float(np.max(np.abs(x.detach().cpu().numpy() - sol.x))) <= 1e-5
+    for nm in OG.MULTI_PARAMS:
+        grad = t[nm].grad.detach().cpu().numpy()
+        delta = rng.standard_normal(grad.shape)
+        a = float(np.sum(grad * delta))
+        b = OG.directional_vjp(prob, sol, g, nm, delta)
+        scale = float(np.linalg.norm(grad) * np.linalg.norm(delta))
+        assert abs(a - b) <= TOL_GRAD * abs(b) + 1e-7 * scale, (nm, a, b)

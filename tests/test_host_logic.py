@@ -1,9 +1,11 @@
 """Host-side logic without a GPU: the synthetic input recipe, the packed batch
-layout and the benchmark's algorithmic-byte count."""
+layout, the benchmark's algorithmic-byte count, the adjoint dispatch of
+BatchRunner and the argument checks of the differentiable solves."""
 import os
 import sys
 
 import numpy as np
+import pytest
 
 from paper_2604_22625_gb300 import api, synthetic as S
 
@@ -132,3 +134,14 @@ def test_batchrunner_backward_dispatch(monkeypatch):
     assert br.bstatus.tolist() == [10, 11, 12, 13]
     # one single-period launch; the multi-period sequence for rmax = 3 (4 + 1) = 15 rows
     assert br.backward_launches() == 1 + (2 + 2 * 1 + 2 + 6 + 6000 + 7)
+
+
+def test_multi_autograd_rejects_a_single_period_shape():
+    """FlashFolioMultiFn checks the T x n shape of alpha before any library call."""
+    import torch
+
+    from paper_2604_22625_gb300.autograd import SolveParams, solve_diff_multi
+    n, k = 5, 2
+    z = torch.zeros
+    with pytest.raises(ValueError):
+        solve_diff_multi(z(n), z(n, k), z(n), z(n), z(n), z(n), z(n), z(k), z(0, n), z(0), z(0), SolveParams())
