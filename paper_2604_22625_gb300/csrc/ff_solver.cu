@@ -852,6 +852,16 @@ __device__ void reduce_chunk(Ctx<M, S>& c, int p0, int pc, const double* a0, con
     }
 }
 
+// FP64 reduce of the KKT check in chunks of at most 4 periods: its
+// accumulator (4 rows x 2 vectors x PCT doubles per thread) would otherwise
+// take 128 registers at PCT = 8 and force spills in the multi-period variant
+template <int PCMAX, class M, class S>
+__device__ void reduce_chunk_f64(Ctx<M, S>& c, int p0, int pc, const double* f1) {
+    if (pc <= 1) reduce_chunk_t<1, double>(c, p0, pc, nullptr, nullptr, nullptr, f1, true);
+    else if (pc <= 2) reduce_chunk_t<2, double>(c, p0, pc, nullptr, nullptr, nullptr, f1, true);
+    else reduce_chunk_t<4, double>(c, p0, pc, nullptr, nullptr, nullptr, f1, true);
+}
+
 // ---------------------------------------------------------------------------
 // expand pass: for every local asset i and period p < Pv,
 //   epi(i, p, (F wF_p)_i, (A^T wA_p)_i)     with wF (Pv x k), wA (Pv x m)
@@ -1621,15 +1631,19 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                 __syncthreads();
                 if (check) {
                     // F^T (x_bar - c) for the KKT check in FP64 products: the objective
-                    // term kappa u^T Omega u must not carry the FP32 product error
-                    reduce_chunk<PCMAX, double>(c, p0, pc, (const double*)nullptr, (const double*)nullptr,
-                                                (const double*)nullptr, c.I.xb, true);
-                    team_reduce<false>(cl, c.vpart, c.vout, pc * Lr, G, g);
-                    for (int e = c.tid; e < pc * k; e += kThreads) {
-                        const int q = e / k, jj = e % k;
-                        c.ub[(p0 + q) * k + jj] = c.vout[q * Lr + 2 * m + k + jj];
+                    // term kappa u^T Omega u must not carry the FP32 product error.
+                    // Sub-chunks of <= 4 periods; their count depends on pc only, so
+                    // every CTA of the cluster takes the same team reductions
+                    for (int s0 = 0; s0 < pc; s0 += 4) {
+                        const int sc = min(4, pc - s0);
+                        reduce_chunk_f64<PCMAX>(c, p0 + s0, sc, c.I.xb);
+                        team_reduce<false>(cl, c.vpart, c.vout, sc * Lr, G, g);
+                        for (int e = c.tid; e < sc * k; e += kThreads) {
+                            const int q = e / k, jj = e % k;
+                            c.ub[(p0 + s0 + q) * k + jj] = c.vout[q * Lr + 2 * m + k + jj];
+                        }
+                        __syncthreads();
                     }
-                    __syncthreads();
                 }
             }
             // rotate iterate buffers: x <- x_new, y_D <- y_D new
