@@ -734,7 +734,7 @@ const char* ff_status_string(int code) {
     }
 }
 
-int ff_version(void) { return 100; }
+int ff_version(void) { return 200; }   // 0.2.0: ff_grads.wT, multi-period adjoint
 
 const char* ff_last_error(void) { return ff::g_last_error; }
 
