@@ -154,3 +154,21 @@ def test_batch_count_limit(lib):
     o = _lib.default_options()
     rc = _lib.ff_solve_batch(probs, 70000, o, 0, 0, 4096, [4096] * 70000)
     assert rc == _lib.FF_ERR_UNSUPPORTED
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """Without the built library the binding raises; there is no CPU fallback
+    (the package never routes a solve through the oracle)."""
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        _lib.load(str(tmp_path / "libflashfolio.so"))
+
+
+def test_package_does_not_import_the_oracle():
+    """Only tests, the smoke check and the bench's CPU legs may use oracle/."""
+    pkg = os.path.join(ROOT, "paper_2604_22625_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import oracle|from oracle)", src, re.M), f
