@@ -108,7 +108,7 @@ __device__ double block_reduce(double v, double* red) {
     __syncthreads();
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
-    double t = kMax ? 0.0 : 0.0;
+    double t = 0.0;   // the maxima taken here are of magnitudes (>= 0)
     for (int w = 0; w < kRT / 32; ++w) t = kMax ? fmax(t, red[w]) : t + red[w];
     __syncthreads();
     return t;
