@@ -19,9 +19,7 @@ import oracle
 from oracle import grad as OG
 from paper_2604_22625_gb300 import synthetic as S
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="multi-period adjoint kernels await their first GPU run; the algorithm "
-                                      "is checked on the CPU by a serial emulation of the kernels")]
+pytestmark = pytest.mark.gpu
 
 TOL_GRAD = 1e-4
 

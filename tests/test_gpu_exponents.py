@@ -14,8 +14,7 @@ from paper_2604_22625_gb300 import synthetic as S
 
 from test_gpu_parity import TOL_SOLVE, _compare
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="exponents other than 1.5 await their first GPU run")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
