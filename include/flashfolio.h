@@ -134,6 +134,11 @@ typedef struct ff_options {
     double  restart_artificial; /* also restart once the iterations since the last restart
                                    reach this share of all iterations so far (0 = off);
                                    default 0.36 */
+    int32_t test_expire_first_wait; /* testing aid, default 0.  1: the first wait of each
+                                   instance for a panel-tile copy counts as expired (the copy
+                                   itself is valid and is let land before the team moves on),
+                                   so the instance ends with FF_STALLED; this exercises the
+                                   bounded-wait path without a faulty copy */
 } ff_options;
 
 /* Per-instance outcome, written to DEVICE memory by the solve calls. */
@@ -144,8 +149,7 @@ typedef struct ff_result {
     double  rel_kkt;            /* max(r_primal, r_dual, r_gap) at the returned point */
     double  r_primal, r_dual, r_gap;   /* r_primal = ||Ax - clip(Ax)|| / (||Ax|| + ||clip(Ax)||);
                                    r_dual = ||x - Proj(x - grad f - K^T y)|| /
-                                   (||x|| + ||grad f|| + ||K^T y||); r_gap = |P - D| /
-                                   max(|P| + |D|, Phi), Phi = sum |alpha_i x_i| + risk + cost */
+                                   (||x|| + ||grad f|| + ||K^T y||); r_gap = |P - D| / (|P| + |D|) */
     double  primal_obj;         /* scaled minimisation objective P(x) = -(Eq. 1)/GMV (+ constant, multi) */
     double  dual_obj;           /* the matching dual bound */
     double  paper_obj;          /* Eq. 1 / Eq. 4 in the paper's units (maximised) */
@@ -156,6 +160,9 @@ typedef struct ff_result {
     double  phase_seconds[6];   /* device time by phase (rank 0 of the team): setup,
                                    expand pass, l1 thresholds, elementwise prox,
                                    reduce pass + team sums, KKT checks */
+    double  term_scale;         /* Phi = sum |alpha_i x_i| + risk + trading cost at the returned
+                                   point (scaled units): the magnitude of the objective's terms,
+                                   against which |P - D| can also be read */
 } ff_result;
 
 /* Fill *o with the defaults listed above. */
@@ -202,7 +209,9 @@ int ff_solve_batch(const ff_problem* probs, int count, const ff_options* o, void
  *
  * Arguments, layouts and results are those of ff_solve_single (the caller
  * still passes the problem arrays, result_dev and the outputs as device
- * pointers).  The workspace is a file-scope device array of
+ * pointers); the cluster size is chosen as there.  options.reuse_workspace
+ * has no effect: every call writes the instance record and repacks the
+ * problem into the array.  The workspace is a file-scope device array of
  * FF_STATIC_WORKSPACE_BYTES inside this library, which every GPU that loads
  * the library holds until the process exits.  The call makes no cudaMalloc,
  * cudaFree or other allocating call on the host or the device.

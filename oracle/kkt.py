@@ -15,12 +15,13 @@ project reports instead:
 
     r_p   = ||Ax - clip(Ax, L, U)|| / (||Ax|| + ||clip(Ax, L, U)||)
     r_d   = ||x - Proj_B1(x - (grad f(x) + K^T y))|| / (||x|| + ||grad f(x)|| + ||K^T y||)
-    r_gap = |P(x) - D(y; x)| / max(|P(x)| + |D(y; x)|, Phi(x))
-with Phi(x) = sum |alpha_i x_i| + kappa sum_p (x_p - c)^T Sigma_p (x_p - c) + phi(Delta x + b),
-the magnitude of the objective's terms: where the optimal value nearly cancels
-(|P| much smaller than its terms) the gap is measured against the scale at
-which the terms themselves are computed, not against the cancelled value;
-with the weak-duality bound (valid for every x, y)
+    r_gap = |P(x) - D(y; x)| / (|P(x)| + |D(y; x)|)
+(purely relative, with no "1 +": the scaled objectives are of order 1e-4 to
+1e-3, so an absolute floor would hide the gap).  Reported beside it, not part
+of rel_kkt: r_gap_terms = |P - D| / max(|P| + |D|, Phi(x)) with
+Phi(x) = sum |alpha_i x_i| + kappa sum_p (x_p - c)^T Sigma_p (x_p - c) + phi(Delta x + b),
+the magnitude of the objective's terms; with the weak-duality bound (valid for
+every x, y)
     D(y; x) = f(x) - <grad f(x), x> - g*(-grad f(x) - K^T y) - h_A*(y_A) - h_D*(y_D),
     g*(v) = sum_p ||v_p||_inf,  h_A*(y) = sum U y^+ - L y^-,
     h_D*(y) = -<y, b> + sum phi*(y).
@@ -45,6 +46,8 @@ class KKT:
     r_primal: float
     r_dual: float
     r_gap: float
+    r_gap_terms: float = float("nan")   # |P - D| / max(|P| + |D|, Phi): not part of rel_kkt
+    term_scale: float = float("nan")    # Phi(x)
 
     @property
     def rel_kkt(self) -> float:
@@ -101,8 +104,10 @@ def evaluate(sc: Scaled, x, yA, yD) -> KKT:
     r_d = np.linalg.norm(x - proj) / (np.linalg.norm(x) + np.linalg.norm(g) + np.linalg.norm(Kty) + TINY)
     P_ = sc.objective(x)
     D_ = dual_bound(sc, x, yA, yD)
-    r_gap = abs(P_ - D_) / (max(abs(P_) + abs(D_), term_scale(sc, x)) + TINY)
-    return KKT(P_, D_, float(r_p), float(r_d), float(r_gap))
+    r_gap = abs(P_ - D_) / (abs(P_) + abs(D_) + TINY)
+    phi = term_scale(sc, x)
+    r_gap_terms = abs(P_ - D_) / (max(abs(P_) + abs(D_), phi) + TINY)
+    return KKT(P_, D_, float(r_p), float(r_d), float(r_gap), float(r_gap_terms), float(phi))
 
 
 def strong_convexity_modulus(sc: Scaled) -> float:

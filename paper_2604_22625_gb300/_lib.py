@@ -56,7 +56,7 @@ class ff_options(C.Structure):
                 ("restart_sufficient", C.c_double), ("restart_necessary", C.c_double),
                 ("step_fraction", C.c_double), ("cluster_size", C.c_int32), ("max_teams", C.c_int32),
                 ("beta", C.c_double), ("reuse_workspace", C.c_int32), ("cta_work", C.c_double),
-                ("restart_artificial", C.c_double)]
+                ("restart_artificial", C.c_double), ("test_expire_first_wait", C.c_int32)]
 
 
 class ff_grads(C.Structure):
@@ -70,7 +70,7 @@ class ff_result(C.Structure):
                 ("r_gap", C.c_double), ("primal_obj", C.c_double), ("dual_obj", C.c_double),
                 ("paper_obj", C.c_double), ("fixed_point_res", C.c_double), ("seconds", C.c_double),
                 ("lipschitz", C.c_double), ("threshold_rounds", C.c_int64),
-                ("phase_seconds", C.c_double * 6)]
+                ("phase_seconds", C.c_double * 6), ("term_scale", C.c_double)]
 
 
 RESULT_DTYPE = np.dtype([(name, {C.c_int32: np.int32, C.c_int64: np.int64, C.c_double: np.float64}[ct])

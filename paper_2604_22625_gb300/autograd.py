@@ -14,6 +14,13 @@ gradient for w_T.
 
 All tensors live on one CUDA device with one floating dtype (float32 or
 float64); no arithmetic of the method runs in Python.
+
+Implicit differentiation is valid only at a solution: unless
+``SolveParams.check_status`` is False, the forward pass reads the solve's
+ff_result.status (one device-to-host read) and raises ``SolveError`` unless
+it is FF_CONVERGED, and the backward pass raises ``SolveError`` when the
+adjoint reports a degenerate active set (non-positive pivot or curvature) or
+an iteration limit.
 """
 from __future__ import annotations
 
@@ -36,6 +43,32 @@ class SolveParams:
     tol: float = 1e-7
     max_iter: int = 400000
     time_limit: float = 360.0
+    check_status: bool = True
+
+
+class SolveError(RuntimeError):
+    """A forward solve that did not converge, or an adjoint that failed."""
+
+
+def _forward_status(res: torch.Tensor) -> int:
+    return int(res[:4].view(torch.int32).item())
+
+
+def _check_forward(res: torch.Tensor, prm: SolveParams, what: str) -> int:
+    st = _forward_status(res)
+    if prm.check_status and st != L.FF_CONVERGED:
+        raise SolveError(f"{what}: the solve stopped with status {L.STATUS_NAMES.get(st, st)} "
+                         f"(implicit differentiation needs a converged solution)")
+    return st
+
+
+def _check_backward(status: torch.Tensor, prm: SolveParams, what: str) -> None:
+    if not prm.check_status:
+        return
+    st = int(status.abs().max().item())
+    if st != 0:
+        raise SolveError(f"{what}: adjoint status {st} (1/2: non-positive pivot, 3: iteration limit, "
+                         f"4: non-positive curvature; a degenerate active set)")
 
 
 _PREC = {"f64": L.FF_PREC_F64, "f32": L.FF_PREC_F32, "bf16": L.FF_PREC_BF16}
@@ -82,6 +115,7 @@ class FlashFolioFn(torch.autograd.Function):
             raise RuntimeError(f"ff_solve_single: {L.ff_status_string(rc)} {L.ff_last_error()}")
         ctx.prm = prm
         ctx.result = res
+        ctx.status = _check_forward(res, prm, "ff_solve_single")
         ctx.save_for_backward(t["alpha"], t["F"], t["D"], t["s"], t["q"], t["w0"], t["Omega"], t["A"], t["L"],
                               t["U"], w, yA, yD)
         return w
@@ -107,7 +141,7 @@ class FlashFolioFn(torch.autograd.Function):
                                   ws.data_ptr(), ws_bytes, status.data_ptr(), stream.cuda_stream)
         if rc != L.FF_OK:
             raise RuntimeError(f"ff_backward_single: {L.ff_status_string(rc)} {L.ff_last_error()}")
-        ctx.status = status
+        _check_backward(status, ctx.prm, "ff_backward_single")
         return (outs["alpha"], outs["F"], outs["D"], outs["s"], outs["q"], outs["w0"], None, None, None, None, None)
 
 
@@ -142,6 +176,7 @@ class FlashFolioMultiFn(torch.autograd.Function):
             raise RuntimeError(f"ff_solve_multi: {L.ff_status_string(rc)} {L.ff_last_error()}")
         ctx.prm = prm
         ctx.result = res
+        ctx.status = _check_forward(res, prm, "ff_solve_multi")
         ctx.save_for_backward(*[t[nm] for nm in _MULTI_IN], w, yA, yD)
         return w
 
@@ -166,7 +201,7 @@ class FlashFolioMultiFn(torch.autograd.Function):
                            ws.data_ptr(), ws_bytes, status.data_ptr(), stream.cuda_stream)
         if rc != L.FF_OK:
             raise RuntimeError(f"ff_backward: {L.ff_status_string(rc)} {L.ff_last_error()}")
-        ctx.status = status
+        _check_backward(status, ctx.prm, "ff_backward")
         return tuple(outs[nm] for nm in _MULTI_GRAD) + (None, None, None, None, None)
 
 

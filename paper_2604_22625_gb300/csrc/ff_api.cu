@@ -148,6 +148,7 @@ void fill_defaults(ff_options* o) {
     o->restart_artificial = 0.36;
     o->cluster_size = 0;
     o->max_teams = 0;
+    o->test_expire_first_wait = 0;
 }
 
 bool valid_options(const ff_options& o) {
@@ -166,6 +167,7 @@ bool valid_options(const ff_options& o) {
     if (o.reuse_workspace < 0 || o.reuse_workspace > 2) return false;
     if (!(o.cta_work >= 1.0)) return false;
     if (!(o.restart_artificial >= 0 && o.restart_artificial < 1)) return false;
+    if (o.test_expire_first_wait != 0 && o.test_expire_first_wait != 1) return false;
     return true;
 }
 
@@ -306,13 +308,6 @@ Inst<M, S> carve(const ff_problem& p, const Sizes& s, unsigned char*& cur, void*
     return I;
 }
 
-int auto_cluster(const Sizes& s, int count) {
-    if (count > 1) return 1;
-    int g = 1;
-    while (g < 16 && (long long)s.n * s.P > (long long)g * 384) g *= 2;
-    return g;
-}
-
 // Cluster size of every instance of a batch.  Each instance starts with the
 // smallest power of two G that keeps its asset-periods per CTA at or below
 // cta_work; while the whole batch would occupy fewer than half the SMs, the
@@ -391,6 +386,7 @@ Params make_params(const ff_options& o) {
     prm.step_fraction = o.step_fraction;
     prm.beta = o.beta;
     prm.power_iters = 60;
+    prm.expire_first_wait = o.test_expire_first_wait;
     prm.queue = nullptr;
     return prm;
 }
@@ -552,8 +548,9 @@ int dispatch(const ff_problem* probs, int count, const ff_options* o_in, void* w
 // ---------------------------------------------------------------------------
 // ff_solve_single_static: the single-period solve on a workspace that lives in
 // this library's own device memory (g_static_ws below), for callers that must
-// not allocate.  Nothing here allocates: the instance record is staged on the
-// host stack and the workspace address comes from cudaGetSymbolAddress.
+// not allocate.  Nothing here allocates: the instance record and the problem
+// record reach the array as kernel parameters (store_records_kernel), and the
+// workspace address comes from cudaGetSymbolAddress.
 // ---------------------------------------------------------------------------
 constexpr size_t c_a256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -582,11 +579,25 @@ void* static_workspace() {
     return g_static_ptr[dev];
 }
 
+// Writes the instance record and the problem record into device memory; they
+// travel as kernel parameters, so no host buffer has to outlive the call.
+template <class M, class S>
+__global__ void store_records_kernel(Inst<M, S>* inst_dst, Inst<M, S> inst, ff_problem* prob_dst, ff_problem prob) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *inst_dst = inst;
+        *prob_dst = prob;
+    }
+}
+
 template <class M, class S>
 int run_single_static(const ff_problem& p, const ff_options& o, ff_result* res, void* w_out, void* yA_out,
                       void* yD_out, cudaStream_t stream) {
     const Sizes sz = sizes_of(p, o.precision);
-    if (!supported(sz, p.omega_diag, o.precision)) return FF_ERR_UNSUPPORTED;
+    if (!supported(sz, p.omega_diag, o.precision)) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "problem shape not supported by the kernels (n %d, k %d, m %d)", p.n, p.k, p.m);
+        return FF_ERR_UNSUPPORTED;
+    }
     constexpr size_t kInstBytes = c_a256(sizeof(Inst<M, S>));
     constexpr size_t kStage = kInstBytes + c_a256(sizeof(ff_problem));
     const size_t need = kStage + kQueueBytes + inst_bytes(sz, p.omega_diag, o.precision);
@@ -596,31 +607,42 @@ int run_single_static(const ff_problem& p, const ff_options& o, ff_result* res, 
                  (size_t)FF_STATIC_WORKSPACE_BYTES);
         return FF_ERR_WORKSPACE;
     }
+    // cluster size as ff_solve_single chooses it (cta_work, then spread over
+    // the SMs), halved while such a cluster cannot be resident; decided
+    // before anything is enqueued
+    std::vector<int> Gv;
+    if (o.cluster_size > 0) Gv.assign(1, o.cluster_size);
+    else choose_clusters(std::vector<Sizes>(1, sz), o.cta_work, sm_count(), Gv);
+    int G = Gv[0];
+    const size_t smem = smem_of(sz, o.precision);
+    int maxc = 0;
+    for (;;) {
+        cudaError_t e = max_teams<M, S>(G, smem, true, &maxc);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy query of the solver kernel");
+        if (maxc >= 1 || G == 1 || o.cluster_size > 0) break;
+        G /= 2;
+    }
+    if (maxc < 1) {
+        snprintf(g_last_error, sizeof(g_last_error),
+                 "a cluster of %d CTAs with %zu bytes of shared memory each cannot be resident", G, smem);
+        return FF_ERR_UNSUPPORTED;
+    }
     unsigned char* base = (unsigned char*)static_workspace();
     if (!base) return FF_ERR_CUDA;
-    alignas(16) unsigned char staging[kStage];
-    memset(staging, 0, sizeof(staging));
     unsigned char* cur = base + kStage + kQueueBytes;
-    Inst<M, S> inst = carve<M, S>(p, sz, cur, w_out, yA_out, yD_out, res);
-    memcpy(staging, &inst, sizeof(inst));
-    memcpy(staging + kInstBytes, &p, sizeof(ff_problem));
-    // every region the solver reads is written by the repack or by the
+    const Inst<M, S> inst = carve<M, S>(p, sz, cur, w_out, yA_out, yD_out, res);
+    Inst<M, S>* table_dev = (Inst<M, S>*)base;
+    ff_problem* prob_dev = (ff_problem*)(base + kInstBytes);
+    // every region the solver reads is written here, by the repack or by the
     // solver's own initialisation, so nothing has to be cleared between calls
-    cudaError_t e = cudaMemcpyAsync(base, staging, kStage, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "copy of the instance record");
-    const Inst<M, S>* table_dev = (const Inst<M, S>*)base;
-    const ff_problem* prob_dev = (const ff_problem*)(base + kInstBytes);
+    store_records_kernel<M, S><<<1, 32, 0, stream>>>(table_dev, inst, prob_dev, p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "record store launch");
     long long maxel = std::max((long long)sz.tl.ntile * sz.tl.Rp * sz.tl.CH, (long long)sz.np * (sz.P + sz.R));
     const int bx = (int)std::min<long long>(64, (maxel + 255) / 256);
     repack_batch_kernel<M, S><<<dim3((unsigned)std::max(bx, 1), 1u), 256, 0, stream>>>(prob_dev, table_dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "repack launch");
-    const size_t smem = smem_of(sz, o.precision);
-    const int G = o.cluster_size > 0 ? o.cluster_size : auto_cluster(sz, 1);
-    int maxc = 0;
-    e = max_teams<M, S>(G, smem, true, &maxc);
-    if (e != cudaSuccess) return cuda_fail(e, "occupancy query of the solver kernel");
-    if (maxc < 1) return FF_ERR_UNSUPPORTED;
     int* queue_dev = (int*)(base + kStage);
     e = cudaMemsetAsync(queue_dev, 0, kQueueBytes, stream);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");

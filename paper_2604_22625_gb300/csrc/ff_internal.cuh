@@ -15,8 +15,7 @@ constexpr int kPC = 8;                 // periods processed together in a matvec
 constexpr int kCand = 8;               // threshold candidates per period and search round
 constexpr int kMaxRounds = 16;         // threshold search rounds per projection
 constexpr int kMaxCluster = 16;
-constexpr int kSingleCtasPerSm = 1;
-constexpr int kStallChecks = 48;       // checks without halving the KKT before FP64 escalation    // resident CTAs per SM the single-period variant is built for
+constexpr int kSingleCtasPerSm = 1;    // resident CTAs per SM the single-period variant is built for
 
 constexpr int kStages = 3;             // bulk-copy ring stages per CTA
 constexpr int kMaxTileBytes = 48 * 1024;
@@ -93,6 +92,7 @@ struct Params {
     double step_fraction;
     double beta;
     int power_iters;
+    int expire_first_wait;   // test hook (ff_options.test_expire_first_wait)
     int* queue;          // device counter of the next instance (zero at launch); teams take
                          // instances from it in table order
 };

@@ -160,7 +160,13 @@ struct Pipe {
     int inflight;             // copies issued and not yet consumed
     unsigned phase;           // bit s: parity of the phase stage s completes next
     int* err;                 // shared flag: a bounded wait expired
+    int frozen;               // after an expired wait: no copy is issued and no phase flipped
+                              // until pipe_drain has let the copies in flight land
+    int waits;                // waits of the current instance (the test hook expires the first)
+    int expire_first;         // test hook: treat the instance's first wait as expired
 };
+
+constexpr int kWaitSpins = 1 << 22;    // try_wait polls of one wait before it counts as expired
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
@@ -177,8 +183,9 @@ __device__ __forceinline__ void pipe_init(Pipe& pp) {
 }
 
 // Issue the copy of `bytes` from global `src` into the tail stage.  Called by
-// every thread (uniform), performed by thread 0.
+// every thread (uniform), performed by thread 0.  A frozen ring issues nothing.
 __device__ __forceinline__ void pipe_issue(Pipe& pp, const void* src, unsigned bytes) {
+    if (pp.frozen) return;
     if (threadIdx.x == 0) {
         const unsigned bar = smem_u32(&pp.bars[pp.tail]);
         const unsigned dst = smem_u32(pp.ring + (size_t)pp.tail * pp.stride);
@@ -195,6 +202,7 @@ __device__ __forceinline__ void pipe_issue(Pipe& pp, const void* src, unsigned b
 // copy q moves bytes[q] from src[q] to the stage offset off[q].
 __device__ __forceinline__ void pipe_issue_n(Pipe& pp, int nc, const void* const* src, const unsigned* off,
                                              const unsigned* bytes) {
+    if (pp.frozen) return;
     if (threadIdx.x == 0) {
         unsigned total = 0;
         for (int q = 0; q < nc; ++q) total += bytes[q];
@@ -211,14 +219,12 @@ __device__ __forceinline__ void pipe_issue_n(Pipe& pp, int nc, const void* const
     ++pp.inflight;
 }
 
-// Wait (bounded) until the head stage has landed; returns its shared address.
-// On expiry the shared error flag is set and the stage is used as it is (the
-// instance then ends with FF_STALLED at its next check).
-__device__ __forceinline__ const unsigned char* pipe_wait(Pipe& pp) {
-    const unsigned bar = smem_u32(&pp.bars[pp.head]);
-    const unsigned parity = (pp.phase >> pp.head) & 1u;
+// Poll the barrier of stage `st` for the phase of parity `parity`, at most
+// `spins` times; true once that phase has completed.
+__device__ __forceinline__ bool bar_poll(const Pipe& pp, int st, unsigned parity, int spins) {
+    const unsigned bar = smem_u32(&pp.bars[st]);
     unsigned done = 0;
-    for (int spin = 0; spin < (1 << 22); ++spin) {
+    for (int spin = 0; spin < spins; ++spin) {
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
@@ -226,24 +232,50 @@ __device__ __forceinline__ const unsigned char* pipe_wait(Pipe& pp) {
             : "memory");
         if (done) break;
     }
-    if (!done) *pp.err = 1;
-    return pp.ring + (size_t)pp.head * pp.stride;
+    return done != 0;
 }
 
-// The head stage has been read by every thread (caller synchronised): move on.
+// Wait (bounded) until the head stage has landed; returns its shared address.
+// On expiry the shared error flag is set and the stage is used as it is; the
+// next pipe_pop then freezes the ring (the instance ends with FF_STALLED at its
+// next check, which every CTA of the team takes together).  A frozen ring
+// returns at once: its data are not used for a result.
+__device__ __forceinline__ const unsigned char* pipe_wait(Pipe& pp) {
+    const unsigned char* stage = pp.ring + (size_t)pp.head * pp.stride;
+    if (pp.frozen) return stage;
+    const bool expire = pp.expire_first && pp.waits == 0;
+    ++pp.waits;
+    if (expire || !bar_poll(pp, pp.head, (pp.phase >> pp.head) & 1u, kWaitSpins)) *pp.err = 1;
+    return stage;
+}
+
+// The head stage has been read by every thread (caller synchronised, so every
+// thread sees the same error flag): move on.  After an expired wait the ring
+// freezes instead: the stage's phase is not flipped (its copy may still be
+// landing), so the bookkeeping keeps matching the barriers for pipe_drain.
 __device__ __forceinline__ void pipe_pop(Pipe& pp) {
+    if (pp.frozen) return;
+    if (*pp.err) { pp.frozen = 1; return; }
     pp.phase ^= 1u << pp.head;
     pp.head = pp.head + 1 == kStages ? 0 : pp.head + 1;
     --pp.inflight;
 }
 
-// Before the CTA leaves an instance on an error, let copies still in flight land.
-__device__ void pipe_drain(Pipe& pp) {
+// Before the team leaves an instance: let every copy still in flight land
+// (bounded waits on the phases the bookkeeping expects) and unfreeze the
+// ring.  Copies of valid global memory complete in microseconds, so the bound
+// is only reached on a hardware fault; the return value (false then) is the
+// same on every thread of the CTA.
+__device__ bool pipe_drain(Pipe& pp) {
+    bool ok = true;
     while (pp.inflight > 0) {
-        pipe_wait(pp);
-        __syncthreads();
-        pipe_pop(pp);
+        ok = bar_poll(pp, pp.head, (pp.phase >> pp.head) & 1u, kWaitSpins) && ok;
+        pp.phase ^= 1u << pp.head;
+        pp.head = pp.head + 1 == kStages ? 0 : pp.head + 1;
+        --pp.inflight;
     }
+    pp.frozen = 0;
+    return __syncthreads_and(ok ? 1 : 0) != 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1238,6 +1270,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
     constexpr bool kIncr = std::is_same<M, float>::value;
     __shared__ int next_s;
     __shared__ int pipe_err_s;
+    __shared__ int ring_broken_s;   // a copy never landed: no further copies on this CTA
     Pipe pipe;
     pipe.bars = (unsigned long long*)smem;   // the layout puts the barriers first
     pipe.ring = nullptr;
@@ -1247,7 +1280,10 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
     pipe.inflight = 0;
     pipe.phase = 0;
     pipe.err = &pipe_err_s;
-    if (threadIdx.x == 0) pipe_err_s = 0;
+    pipe.frozen = 0;
+    pipe.waits = 0;
+    pipe.expire_first = prm.expire_first_wait;
+    if (threadIdx.x == 0) { pipe_err_s = 0; ring_broken_s = 0; }
     pipe_init(pipe);
 
     for (;;) {
@@ -1278,8 +1314,10 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         pipe.ring = smem + Ly.ring;
         pipe.stride = Ly.tile_bytes;
         c.pipe = pipe;
+        c.pipe.waits = 0;
+        c.pipe.frozen = ring_broken_s;   // uniform: written before the last cluster barrier
         c.panel_off = (unsigned)Ly.panel_bytes;
-        if (threadIdx.x == 0) pipe_err_s = 0;
+        if (threadIdx.x == 0) pipe_err_s = ring_broken_s;
         c.vpart = (double*)(smem + Ly.vpart);
         c.vout = (double*)(smem + Ly.vout);
         c.spart = (double*)(smem + Ly.spart);
@@ -1433,7 +1471,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         int j = 0, restarts = 0;
         int status = FF_MAX_ITER;
         double r_restart = -1, r_prev = INFINITY, r_last = 0;
-        double res_rel = INFINITY, res_p = 0, res_d = 0, res_g = 0, res_P = 0, res_D = 0;
+        double res_rel = INFINITY, res_p = 0, res_d = 0, res_g = 0, res_P = 0, res_D = 0, res_T = 0;
         for (it = 0; it < prm.max_iter; ++it) {
             const bool check = (it % prm.check_every) == 0;
             const double cj = (double)(j + 1) / (double)(j + 2);
@@ -1788,15 +1826,14 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             const double Dobj = fval - sums[3] - gstar - hA - sums[8];
             const double r_p = sqrt(pin_t) / (sqrt(nAx_t) + sqrt(nCl_t) + 1e-30);
             const double r_d = rd_num / (sqrt(sums[4]) + sqrt(sums[5]) + sqrt(sums[6]) + 1e-30);
-            // gap relative to the larger of |P| + |D| and the magnitude of the
-            // objective's terms (return magnitudes + risk + trading cost), so that
-            // an optimal value that nearly cancels does not demand more precision
-            // than the terms are computed with
+            // purely relative gap |P - D| / (|P| + |D|); the magnitude of the
+            // objective's terms (return magnitudes + risk + trading cost) is
+            // reported beside it (ff_result.term_scale)
             const double phi_terms = sums[10] + sums[9] + kap * fF_t + sums[7];
-            const double r_g = fabs(Pobj - Dobj) / (fmax(fabs(Pobj) + fabs(Dobj), phi_terms) + 1e-30);
+            const double r_g = fabs(Pobj - Dobj) / (fabs(Pobj) + fabs(Dobj) + 1e-30);
             const double rel = fmax(r_p, fmax(r_d, r_g));
             const double fpr = sqrt(sums[0] / tau + sums[1] / sD + rA_t / sA);
-            res_rel = rel; res_p = r_p; res_d = r_d; res_g = r_g; res_P = Pobj; res_D = Dobj;
+            res_rel = rel; res_p = r_p; res_d = r_d; res_g = r_g; res_P = Pobj; res_D = Dobj; res_T = phi_terms;
             r_last = fpr;
             lap(5);
             if (sums[12] > 0) { status = FF_STALLED; break; }
@@ -1829,6 +1866,14 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             }
         }
 
+        // a frozen ring may still have copies landing in its stages: let them
+        // land before the outputs and the next instance (bounded waits)
+        __syncthreads();
+        if (c.pipe.frozen && !ring_broken_s) {
+            const bool ok = pipe_drain(c.pipe);
+            if (!ok && threadIdx.x == 0) ring_broken_s = 1;
+            if (!ok) c.pipe.frozen = 1;
+        }
         // ---- outputs: T(z) of the last check (x_bar, y_bar) -----------------
         __syncthreads();
         for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
@@ -1869,20 +1914,15 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             rs.lipschitz = Lf;
             rs.threshold_rounds = th_rounds;
             for (int q = 0; q < 6; ++q) rs.phase_seconds[q] = ph[q] * 1e-9;
+            rs.term_scale = res_T;
             *c.I.res = rs;
         }
         pipe = c.pipe;
         // the next instance reuses shared memory: every rank must be done with it
         cl.sync();
     }
-    // a copy whose wait expired may still be landing: give it (bounded) time
-    // before the CTA's shared memory is released
-    if (pipe_err_s) {
-        for (int s2 = 0; s2 < kStages; ++s2) {
-            pipe.head = s2;
-            pipe_wait(pipe);
-        }
-    }
+    // every instance drained its ring before the team moved on; only a copy
+    // that never landed (ring_broken_s, a hardware fault) can still be pending
 }
 
 template <class M, class S, int PCMAX>

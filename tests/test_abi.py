@@ -31,10 +31,34 @@ def test_exports(lib):
         assert hasattr(lib, nm), nm
 
 
-def test_struct_sizes_match_header(lib):
-    # ff_result layout mirrors the header (all 8-byte fields after two int32)
-    assert C.sizeof(_lib.ff_result) == 4 + 4 + 8 + 8 * 10 + 8 + 8 * 6
+def test_struct_sizes_match_header(lib, tmp_path):
+    """The ctypes mirrors have the size and field offsets of the header's
+    structs, as a C compiler lays them out (gcc on this host)."""
+    import shutil
+    import subprocess
     assert _lib.RESULT_DTYPE.itemsize == C.sizeof(_lib.ff_result)
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"ff_result": _lib.ff_result, "ff_options": _lib.ff_options, "ff_problem": _lib.ff_problem,
+               "ff_grads": _lib.ff_grads}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "flashfolio.h"', "int main(void) {"]
+    for nm, cls in structs.items():
+        lines.append(f'printf("{nm} %zu\\n", sizeof({nm}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{nm}.{fname} %zu\\n", offsetof({nm}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "abi.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "abi"
+    inc = os.path.join(ROOT, "include")
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True, capture_output=True)
+    out = dict(line.rsplit(" ", 1) for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                               text=True).stdout.splitlines())
+    for nm, cls in structs.items():
+        assert int(out[nm]) == C.sizeof(cls), nm
+        for fname, _ in cls._fields_:
+            assert int(out[f"{nm}.{fname}"]) == getattr(cls, fname).offset, (nm, fname)
 
 
 def test_host_only_calls(lib):

@@ -148,3 +148,24 @@ def test_batched_backward_matches_oracle(torch_mod):
             b = OG.directional_vjp(p, sol, gs[i], nm, delta)
             scale = float(np.linalg.norm(grad) * np.linalg.norm(delta))
             assert abs(a - b) <= TOL_GRAD * abs(b) + 1e-7 * scale, (i, nm, a, b)
+
+
+def test_autograd_raises_on_unconverged_forward():
+    """Implicit differentiation is only valid at a solution: a forward solve
+    stopped by max_iter raises SolveError unless check_status is False."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2604_22625_gb300.autograd import SolveError, SolveParams, solve_diff
+    from paper_2604_22625_gb300.build import build
+    build()
+    prob = S.make_single(200, 8, 71, n_onehot=2)
+    t = {nm: torch.tensor(np.asarray(getattr(prob, nm), dtype=np.float64), device="cuda")
+         for nm in ("alpha", "F", "D", "s", "q", "w0", "A", "L", "U")}
+    t["Omega"] = torch.tensor(np.diag(prob.Omega).copy(), device="cuda")
+    t["alpha"].requires_grad_(True)
+    args = (t["alpha"], t["F"], t["D"], t["s"], t["q"], t["w0"], t["Omega"], t["A"], t["L"], t["U"])
+    with pytest.raises(SolveError):
+        solve_diff(*args, SolveParams(precision="f64", max_iter=1))
+    w = solve_diff(*args, SolveParams(precision="f64", max_iter=1, check_status=False))
+    assert w.shape == (200,)

@@ -10,15 +10,16 @@
 
 The solves run to 2e-7 relative KKT for the same reason as the small parity
 tests (a 1e-6 point is not certified within 1e-5 of w*).  Bars:
-|w - w*|_inf <= 1e-5, relative objective gap <= 1e-6 (relative to the
-magnitude of the objective's terms), the solver's own relative KKT <= 1e-6.
+|w - w*|_inf <= 1e-5, relative objective gap |P(w) - P*| / |P*| <= 1e-6, the
+solver's own relative KKT <= 1e-6.  In the batch the sampled multi-period
+instance is the largest one (most asset-periods), whose cluster group takes
+the largest share of the batch's device time.
 """
 import numpy as np
 import pytest
 
 import oracle
 from oracle import Scaled
-from oracle.kkt import term_scale
 from paper_2604_22625_gb300 import synthetic as S
 
 pytestmark = pytest.mark.gpu
@@ -44,7 +45,7 @@ def _check(prob, x, info):
     sc = Scaled(prob)
     x = np.asarray(x, dtype=np.float64).reshape(sc.P, sc.n)
     err = float(np.max(np.abs(x - ref.x)))
-    gap = abs(sc.objective(x) - ref.obj) / max(abs(ref.obj), term_scale(sc, ref.x))
+    gap = abs(sc.objective(x) - ref.obj) / abs(ref.obj)
     assert err <= 1e-5, (prob.tag, err)
     assert gap <= 1e-6, (prob.tag, gap)
 
@@ -74,6 +75,6 @@ def test_batch_full_sampled(api):
     rng = np.random.default_rng(11)
     singles = [i for i, p in enumerate(probs) if int(p.T) < 2]
     multis = sorted([i for i, p in enumerate(probs) if int(p.T) >= 2], key=lambda i: probs[i].n * probs[i].T)
-    picks = list(rng.choice(singles, 3, replace=False)) + [multis[0]]
+    picks = list(rng.choice(singles, 3, replace=False)) + [multis[-1]]
     for i in picks:
         _check(probs[i].with_F_rounded_bf16(), ws[i], infos[i])

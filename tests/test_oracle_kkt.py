@@ -1,9 +1,11 @@
 """Properties of the oracle's KKT measures (oracle/kkt.py).
 
 * Phi(x) (the magnitude of the objective's terms) is the sum of |alpha_i x_i|,
-  the risk and the trading cost, so it bounds |P(x)| from above;
-* the relative gap with the max(|P| + |D|, Phi) denominator never exceeds the
-  purely relative gap and equals it when |P| + |D| >= Phi;
+  the risk and the trading cost: pinned to a value worked out by hand on a
+  2-asset instance, and it bounds |P(x)| from above;
+* r_gap is the purely relative gap |P - D| / (|P| + |D|) (the relative KKT
+  definition of the hot-path scope); the gap against max(|P| + |D|, Phi),
+  reported beside it, never exceeds it and equals it when |P| + |D| >= Phi;
 * at the oracle optimum every measure is at rounding level, and a feasible
   perturbation of the optimum raises the gap.
 """
@@ -13,6 +15,26 @@ import oracle
 from oracle import Scaled
 from oracle.kkt import dual_bound, evaluate, term_scale
 from paper_2604_22625_gb300 import synthetic as S
+
+
+def _two_assets():
+    """n = 2, k = 1, m = 0, GMV = 1 (kappa = lambda1 = 2), d = 2."""
+    return S.Problem(F=np.array([[1.0], [2.0]]), Omega=np.array([[0.5]]), D=np.array([0.1, 0.2]),
+                     alpha=np.array([0.3, -0.4]), s=np.array([0.01, 0.02]), q=np.array([0.03, 0.04]),
+                     w0=np.array([0.1, -0.2]), A=np.zeros((0, 2)), L=np.zeros(0), U=np.zeros(0),
+                     GMV=1.0, lam1=2.0, lam2=1.0, lam3=1.0, d=2.0)
+
+
+def test_term_scale_hand_value():
+    """At x = (0.2, 0.3): Sigma = 0.5 F F^T + diag(0.1, 0.2) = [[0.6, 1.0], [1.0, 2.2]],
+    x^T Sigma x = 0.024 + 0.12 + 0.198 = 0.342, kappa x^T Sigma x = 0.684;
+    |alpha_1 x_1| + |alpha_2 x_2| = 0.06 + 0.12 = 0.18; trades z = x - w0 = (0.1, 0.5),
+    cost = 0.01*0.1 + 0.03*0.1^2 + 0.02*0.5 + 0.04*0.5^2 = 0.0213.
+    Phi = 0.18 + 0.684 + 0.0213 = 0.8853 and P(x) = 0.06 + 0.684 + 0.0213 = 0.7653."""
+    sc = Scaled(_two_assets())
+    x = np.array([[0.2, 0.3]])
+    assert abs(term_scale(sc, x) - 0.8853) <= 1e-14
+    assert abs(sc.objective(x) - 0.7653) <= 1e-14
 
 
 def test_term_scale_bounds_objective():
@@ -37,9 +59,11 @@ def test_gap_normalisation():
         k = evaluate(sc, x, sol.yA, sol.yD)
         P_, D_ = sc.objective(x), dual_bound(sc, x, sol.yA, sol.yD)
         plain = abs(P_ - D_) / (abs(P_) + abs(D_))
-        assert k.r_gap <= plain * (1 + 1e-12)
+        assert abs(k.r_gap - plain) <= 1e-12 * plain
+        assert k.r_gap_terms <= plain * (1 + 1e-12)
+        assert abs(k.term_scale - term_scale(sc, x)) <= 1e-15 * k.term_scale
         if abs(P_) + abs(D_) >= term_scale(sc, x):
-            assert abs(k.r_gap - plain) <= 1e-12 * plain
+            assert abs(k.r_gap_terms - plain) <= 1e-12 * plain
         assert k.r_gap >= evaluate(sc, sol.x, sol.yA, sol.yD).r_gap
 
 

@@ -49,8 +49,11 @@ def test_static_matches_workspace_entry_two_calls():
     dev = "cuda:0"
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream(dev)
+    # the last case needs about 28.6 MiB of the 32 MiB array and, with n > 6144,
+    # gets 16-CTA clusters (a non-portable cluster size)
     cases = [(S.make_single(2500, 24, 31, n_onehot=8).rounded(np.float32), "f32"),
-             (S.make_single(700, 12, 32, n_onehot=4), "f64")]
+             (S.make_single(700, 12, 32, n_onehot=4), "f64"),
+             (S.make_single(8000, 110, 33, n_onehot=10), "f64")]
     prepared = []
     for prob, prec in cases:
         dtype = torch.float64 if prec == "f64" else torch.float32
@@ -59,36 +62,47 @@ def test_static_matches_workspace_entry_two_calls():
         ws_bytes = L.ff_workspace_size(C.byref(dp.struct), 1, opts)
         assert 0 < ws_bytes <= L.FF_STATIC_WORKSPACE_BYTES
         prepared.append((prob, dp, opts, ws_bytes, dtype))
+    clusters, _ = L.ff_batch_plan(C.byref(prepared[-1][1].struct), 1, prepared[-1][2])
+    assert clusters[0] == 16
 
     def fresh(dp, dtype):
         res = torch.zeros(L.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
         w = torch.full((dp.n,), float("nan"), dtype=dtype, device=dev)
-        return res, w
+        yA = torch.full((max(dp.m, 1),), float("nan"), dtype=dtype, device=dev)
+        yD = torch.full((dp.n,), float("nan"), dtype=dtype, device=dev)
+        return res, w, yA, yD
+
+    def host(res, w, yA, yD, m):
+        return (res.cpu().numpy().view(L.RESULT_DTYPE)[0], w.cpu().numpy().astype(np.float64),
+                yA.cpu().numpy().astype(np.float64)[:m], yD.cpu().numpy().astype(np.float64))
 
     # reference results through the caller-workspace entry point
     refs = []
     for prob, dp, opts, ws_bytes, dtype in prepared:
         ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
-        res, w = fresh(dp, dtype)
-        rc = L.ff_solve_single(dp.struct, opts, ws.data_ptr(), ws_bytes, res.data_ptr(), w.data_ptr(),
-                               0, 0, stream.cuda_stream)
+        out = fresh(dp, dtype)
+        rc = L.ff_solve_single(dp.struct, opts, ws.data_ptr(), ws_bytes, *[t.data_ptr() for t in out],
+                               stream.cuda_stream)
         assert rc == L.FF_OK, L.ff_last_error()
         stream.synchronize()
-        refs.append((res.cpu().numpy().view(L.RESULT_DTYPE)[0], w.cpu().numpy().astype(np.float64)))
+        refs.append(host(*out, dp.m))
 
     # two static calls in a row (the second reuses what the first left behind)
     outs = []
     for prob, dp, opts, ws_bytes, dtype in prepared:
-        res, w = fresh(dp, dtype)
-        rc = L.ff_solve_single_static(dp.struct, opts, res.data_ptr(), w.data_ptr(), 0, 0, stream.cuda_stream)
+        out = fresh(dp, dtype)
+        rc = L.ff_solve_single_static(dp.struct, opts, *[t.data_ptr() for t in out], stream.cuda_stream)
         assert rc == L.FF_OK, L.ff_last_error()
-        outs.append((res, w))
+        outs.append((out, dp.m))
     stream.synchronize()
-    for (rref, wref), (res, w) in zip(refs, outs):
-        rec = res.cpu().numpy().view(L.RESULT_DTYPE)[0]
-        wv = w.cpu().numpy().astype(np.float64)
+    for (rref, wref, yAref, yDref), (out, m) in zip(refs, outs):
+        rec, wv, yA, yD = host(*out, m)
         assert rref["status"] == L.FF_CONVERGED and rec["status"] == L.FF_CONVERGED, (rref, rec)
         assert rec["rel_kkt"] <= TOL_KKT
-        assert np.all(np.isfinite(wv))
+        assert np.all(np.isfinite(wv)) and np.all(np.isfinite(yA)) and np.all(np.isfinite(yD))
         assert float(np.max(np.abs(wv - wref))) <= TOL_W
+        # the multipliers, relative to the largest of each kind
+        for a, b in ((yA, yAref), (yD, yDref)):
+            if b.size:
+                assert float(np.max(np.abs(a - b))) <= TOL_W * float(np.max(np.abs(b))) + 1e-12
         assert abs(rec["primal_obj"] - rref["primal_obj"]) <= 1e-6 * abs(rref["primal_obj"])
