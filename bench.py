@@ -60,7 +60,14 @@ def parse_args(argv=None):
                     "replaying the captured CUDA graph")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain per-instance form")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the CPU baseline sample")
+    ap.add_argument("--tol", type=float, default=TOL, help="relative KKT tolerance of the timed solves")
+    ap.add_argument("--no-oracle-check", action="store_true", help="skip the oracle check of the timed outputs")
+    ap.add_argument("--no-configs", action="store_true", help="skip the per-configuration solves")
+    ap.add_argument("--check-singles", type=int, default=8)
+    ap.add_argument("--check-multis", type=int, default=3)
+    ap.add_argument("--check-workers", type=int, default=4)
+    ap.add_argument("--plain-singles", type=int, default=16)
+    ap.add_argument("--plain-multis", type=int, default=8)
     ap.add_argument("--diff-multi", type=int, default=0, help="differentiation workload: also this many "
                     "multi-period instances (T=50, n=2000, k=60) through the multi-period adjoint")
     return ap.parse_args(argv)
@@ -198,37 +205,128 @@ def dist_init(backend: str):
 
 
 # ---------------------------------------------------------------------------
-# CPU oracle timing (bounded sample)
+# stratified samples of a workload (shared by the oracle check, the plain
+# per-instance form and both CPU baselines)
 # ---------------------------------------------------------------------------
-def oracle_sample_rate(problems, precision, budget_s: float, start: int = 0):
-    """Time the oracle on a stratified sample; return (solves/s estimate for
-    the whole workload, sample description, seconds spent)."""
+def strata(problems, kind: str, count: int):
+    """Indices of ``count`` instances of one kind ("single" / "multi") at the
+    centres of ``count`` equal-count strata of the size order (asset-periods
+    times rows), so that each stratum's instance stands for it."""
+    idx = [i for i, p in enumerate(problems) if (int(p.T) >= 2) == (kind == "multi")]
+    if not idx or count <= 0:
+        return []
+    key = lambda i: (problems[i].F.shape[0] * max(1, int(problems[i].T) - 1) *  # noqa: E731
+                     (problems[i].F.shape[1] + problems[i].A.shape[0]), i)
+    idx.sort(key=key)
+    count = min(count, len(idx))
+    return [idx[min(len(idx) - 1, int((2 * j + 1) * len(idx) / (2 * count)))] for j in range(count)]
+
+
+def extremes(problems, kind: str, count: int):
+    """``count`` instances of one kind spread over the size order, both ends included."""
+    idx = [i for i, p in enumerate(problems) if (int(p.T) >= 2) == (kind == "multi")]
+    if not idx or count <= 0:
+        return []
+    idx.sort(key=lambda i: (problems[i].F.shape[0] * max(1, int(problems[i].T) - 1), i))
+    pos = np.unique(np.round(np.linspace(0, len(idx) - 1, min(count, len(idx)))).astype(int))
+    return [idx[j] for j in pos]
+
+
+# ---------------------------------------------------------------------------
+# the oracle against the GPU's outputs (a spawned process pool: the oracle is
+# CPU work and must not be forked from a process that holds a CUDA context)
+# ---------------------------------------------------------------------------
+def _oracle_check_one(task):
+    """Worker: (tag, problem, precision, x, yA, yD) -> comparison with the oracle."""
     import oracle
-    singles = [p for p in problems if int(p.T) < 2]
-    multis = [p for p in problems if int(p.T) >= 2]
+    from oracle import Scaled
+    from oracle.kkt import evaluate
+    tag, prob, precision, x, yA, yD = task
+    pr = storage_rounded(prob, precision)
+    sc = Scaled(pr)
+    t0 = time.perf_counter()
+    ref = oracle.solve(pr, polish_max_vars=10 ** 7)
+    x = np.asarray(x, dtype=np.float64).reshape(sc.P, sc.n)
+    out = {"tag": tag, "err_inf": float(np.max(np.abs(x - ref.x))),
+           "obj_gap": abs(sc.objective(x) - ref.obj) / abs(ref.obj),
+           "oracle_certified": bool(ref.polished), "oracle_rel_kkt": float(ref.kkt.rel_kkt),
+           "oracle_s": time.perf_counter() - t0}
+    if yA is not None and yD is not None:
+        k = evaluate(sc, x, yA, yD)
+        out["rel_kkt"] = float(k.rel_kkt)
+    return out
+
+
+def _oracle_time_one(task):
+    """Worker: seconds of one oracle solve."""
+    import oracle
+    prob, precision = task
+    t0 = time.perf_counter()
+    oracle.solve(storage_rounded(prob, precision))
+    return time.perf_counter() - t0
+
+
+def spawn_pool(workers: int):
+    import multiprocessing as mp
+    return mp.get_context("spawn").Pool(processes=workers)
+
+
+def summarize_check(rows, bars=(1e-5, 1e-6)):
+    """oracle_check block of the bench line."""
+    if not rows:
+        return None
+    return {"n": len(rows), "max_err_inf": max(r["err_inf"] for r in rows),
+            "max_obj_gap_strict": max(r["obj_gap"] for r in rows),
+            "max_rel_kkt_strict": max((r.get("rel_kkt", float("nan")) for r in rows), default=None),
+            "within_bars": all(r["err_inf"] <= bars[0] and r["obj_gap"] <= bars[1] for r in rows),
+            "oracle_certified": sum(1 for r in rows if r["oracle_certified"]),
+            "instances": rows}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (stratified sample; the same sample in both arms)
+# ---------------------------------------------------------------------------
+CPU_SINGLES = 4
+CPU_MULTIS = 4
+
+
+def cpu_sample(problems):
+    """The instances the CPU baselines time: CPU_SINGLES single-period and
+    CPU_MULTIS multi-period instances at the centres of equal-count size strata."""
+    return strata(problems, "single", CPU_SINGLES), strata(problems, "multi", CPU_MULTIS)
+
+
+def cpu_rate(problems, ts, tm):
+    """Whole-workload rate from the stratum means: N / (N_s mean_s + N_m mean_m)."""
+    ns = sum(1 for p in problems if int(p.T) < 2)
+    nm = len(problems) - ns
+    est = ns * (statistics.mean(ts) if ts else 0.0) + nm * (statistics.mean(tm) if tm else 0.0)
+    return len(problems) / est if est > 0 else 0.0
+
+
+def cpu_sample_desc(problems, si, mi, reps: str):
+    ns = sum(1 for p in problems if int(p.T) < 2)
+    nm = len(problems) - ns
+    sz = ", ".join(f"T={int(problems[i].T)} n={problems[i].F.shape[0]}" for i in mi)
+    return (f"{len(si)} single-period and {len(mi)} multi-period instances of the workload at the centres of "
+            f"equal-count size strata (multi: {sz}), solved by the FP64 oracle (interior point + active-set "
+            f"polish) {reps}; value = {len(problems)} / ({ns} mean_single + {nm} mean_multi)")
+
+
+def oracle_sample_rate(problems, precision):
+    """Time the oracle once on every instance of the stratified CPU sample."""
+    import oracle
+    si, mi = cpu_sample(problems)
     ts, tm = [], []
     t_begin = time.perf_counter()
-    i = start
-    while True:
-        if singles:
-            p = storage_rounded(singles[i % len(singles)], precision)
+    for grp, acc in ((si, ts), (mi, tm)):
+        for i in grp:
+            p = storage_rounded(problems[i], precision)
             t0 = time.perf_counter()
             oracle.solve(p)
-            ts.append(time.perf_counter() - t0)
-        if multis and (not tm or time.perf_counter() - t_begin < 0.6 * budget_s):
-            p = storage_rounded(multis[i % len(multis)], precision)
-            t0 = time.perf_counter()
-            oracle.solve(p)
-            tm.append(time.perf_counter() - t0)
-        i += 1
-        if time.perf_counter() - t_begin >= budget_s:
-            break
-    est = len(singles) * (statistics.mean(ts) if ts else 0.0) + len(multis) * (statistics.mean(tm) if tm else 0.0)
-    rate = len(problems) / est if est > 0 else 0.0
-    desc = (f"{len(ts)} of {len(singles)} single-period and {len(tm)} of {len(multis)} multi-period instances "
-            f"solved by the FP64 oracle; rate = {len(problems)} / ({len(singles)} mean_single + "
-            f"{len(multis)} mean_multi)")
-    return rate, desc, time.perf_counter() - t_begin, ts, tm
+            acc.append(time.perf_counter() - t0)
+    return (cpu_rate(problems, ts, tm), cpu_sample_desc(problems, si, mi, "once each"),
+            time.perf_counter() - t_begin, ts, tm)
 
 
 def cpu_cores() -> int:
@@ -247,19 +345,19 @@ def run_reference(args):
     if rank != 0:
         return 0
     probs, precision, desc = make_workload(args.workload, 0, args.diff_multi)
-    singles = [p for p in probs if int(p.T) < 2]
-    multis = [p for p in probs if int(p.T) >= 2]
+    si, mi = cpu_sample(probs)
 
     import oracle
 
     def step(i, ts, tm):
-        if singles:
-            p = storage_rounded(singles[i % len(singles)], precision)
+        # one instance of each kind per step, cycling through the stratified sample
+        if si:
+            p = storage_rounded(probs[si[i % len(si)]], precision)
             t0 = time.perf_counter()
             oracle.solve(p)
             ts.append(time.perf_counter() - t0)
-        if multis:
-            p = storage_rounded(multis[i % len(multis)], precision)
+        if mi:
+            p = storage_rounded(probs[mi[i % len(mi)]], precision)
             t0 = time.perf_counter()
             oracle.solve(p)
             tm.append(time.perf_counter() - t0)
@@ -274,12 +372,9 @@ def run_reference(args):
     for i in range(args.steps):
         step(i, ts, tm)
     wall = time.perf_counter() - t0
-    est = len(singles) * (statistics.mean(ts) if ts else 0.0) + len(multis) * (statistics.mean(tm) if tm else 0.0)
-    value = len(probs) / est if est > 0 else 0.0
-    sample = (f"each timed step: one single-period and one multi-period instance of the workload (in "
-              f"workload order from the first), solved by the FP64 oracle (interior point + active-set "
-              f"polish); warm-up steps solve the smallest instance once each; value = {len(probs)} / "
-              f"({len(singles)} mean_single + {len(multis)} mean_multi)")
+    value = cpu_rate(probs, ts, tm)
+    sample = cpu_sample_desc(probs, si, mi, "one single-period and one multi-period instance per timed step, "
+                             "cycling through the sample; warm-up steps solve the smallest instance once each")
     cores = cpu_cores()
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / max(args.steps, 1),
@@ -295,6 +390,20 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def _outputs(runner, i):
+    """(x, yA, yD) of instance i as host arrays (duals None when not kept)."""
+    P, n = runner.P[i], runner.n[i]
+    x = runner.w_dev[int(runner.w_off[i]):int(runner.w_off[i]) + P * n].double().cpu().numpy()
+    if runner.yD_ptrs is None:
+        return x, None, None
+    p = runner.problems[i]
+    m = int(np.asarray(p.A).shape[0])
+    R = int(p.T) if int(p.T) >= 2 else 1
+    yA = runner.yA_dev[int(runner.yA_off[i]):int(runner.yA_off[i]) + P * m].double().cpu().numpy()
+    yD = runner.yD_dev[int(runner.yD_off[i]):int(runner.yD_off[i]) + R * n].double().cpu().numpy()
+    return x, yA, yD
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -305,11 +414,12 @@ def run_ours(args):
     dist = dist_init("nccl")
 
     from paper_2604_22625_gb300 import api
+    from paper_2604_22625_gb300 import synthetic as S
     from paper_2604_22625_gb300.build import build
     build()
 
     probs, precision, desc = make_workload(args.workload, rank, args.diff_multi)
-    opt_kw = {"time_limit": 600.0}
+    opt_kw = {"time_limit": 600.0, "tol": args.tol}
     if args.max_iter > 0:
         opt_kw["max_iter"] = args.max_iter
     diff = args.workload == "diff"
@@ -318,11 +428,11 @@ def run_ours(args):
     tuned = None
     if args.tuned:
         from paper_2604_22625_gb300 import tune
-        tuned = tune.tune(probs, precision=precision, tol=opt_kw.get("tol", TOL),
-                          device=torch.cuda.get_device_name(dev))
+        tuned = tune.tune(probs, precision=precision, tol=opt_kw["tol"], device=torch.cuda.get_device_name(dev))
         opt_kw.update(tuned.options())
-    runner = api.BatchRunner(probs, precision=precision, device=str(dev), duals=diff, **opt_kw)
-    tol_ok = 1e-7 if diff else TOL
+    # duals are kept so that the oracle can evaluate the relative KKT of the timed outputs
+    runner = api.BatchRunner(probs, precision=precision, device=str(dev), duals=True, **opt_kw)
+    tol_ok = opt_kw["tol"]
     if diff:
         runner.prepare_backward()
         gen = torch.Generator(device="cpu").manual_seed(4)
@@ -330,23 +440,52 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     bpi = [algorithmic_bytes_per_iter(p, precision) for p in probs]
     resident_in = runner.h2d_bytes
+    check_oracle = (not args.no_oracle_check) and rank == 0 and args.workload == "batch"
 
     use_graph = not args.no_graph and not diff
     if use_graph:
         runner.capture(stream)
-    if diff:
-        def step(s_):
+    escalated_steps = []
+
+    def step(s_):
+        if use_graph:
+            runner.replay(s_)
+        else:
             runner.run(s_)
+        if diff:
             runner.backward(s_)
-    else:
-        step = runner.replay if use_graph else runner.run
+        escalated_steps.append(runner.finish(s_))
+
     for _ in range(args.warmup):
         step(stream)
     torch.cuda.synchronize(dev)
+    escalated_steps.clear()
+
+    # the oracle check starts on the warm-up outputs (the timed steps solve the
+    # same inputs; their outputs are compared bit for bit below) and runs in
+    # spawned processes while the GPU is timed
+    pool, pending, picks, snap = None, None, [], {}
+    if check_oracle:
+        picks = extremes(probs, "single", args.check_singles) + extremes(probs, "multi", args.check_multis)
+        snap = {i: _outputs(runner, i) for i in picks}
+        workers = max(1, min(len(picks), args.check_workers))
+        threads = max(1, cpu_cores() // workers)
+        saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for v in saved:
+            os.environ[v] = str(threads)
+        pool = spawn_pool(workers)
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
+        tasks = [(probs[i].tag, probs[i], precision, *snap[i]) for i in picks]
+        # largest first, so that the longest oracle solve starts first
+        order = sorted(range(len(tasks)), key=lambda j: -probs[picks[j]].F.shape[0] * max(1, int(probs[picks[j]].T)))
+        pending = [(j, pool.apply_async(_oracle_check_one, (tasks[j],))) for j in order]
 
     sampler = ClockSampler(local)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    solved_steps, iters_steps, kkt_max = [], [], 0.0
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize(dev)
@@ -369,7 +508,10 @@ def run_ours(args):
     iters = [int(i["iterations"]) for i in infos]
     inst_s = [float(i["seconds"]) for i in infos]
     alg_bytes = float(sum(b * it for b, it in zip(bpi, iters)))
+    same_outputs = all(all((a is None and b is None) or np.array_equal(a, b) for a, b in zip(snap[i], _outputs(runner, i)))
+                       for i in picks)
 
+    esc_launches = 2 * max(escalated_steps, default=0)   # repack + solver launch(es) of the FP64 re-solve (bound)
     launches_per_step = 1 + runner.solver_launches() + (runner.backward_launches() if diff else 0)
     t_max = max_over_ranks(dist, dev_s, dev)
     solved_all = sum_over_ranks(dist, float(solved * args.steps), dev)
@@ -399,36 +541,77 @@ def run_ours(args):
             stream.synchronize()
         e2e_s = (time.perf_counter() - t0)
         rec = runner.res_host.numpy().view(api.L.RESULT_DTYPE)
-        e2e_solved = int(sum(1 for r in rec if r["status"] == 0 and r["rel_kkt"] <= TOL))
+        e2e_solved = int(sum(1 for r in rec if r["status"] == 0 and r["rel_kkt"] <= tol_ok))
         e2e_t = max_over_ranks(dist, e2e_s, dev)
         e2e_solved_all = sum_over_ranks(dist, float(e2e_solved * k_e2e), dev)
         e2e = {"value": e2e_solved_all / e2e_t if e2e_t > 0 else 0.0, "unit": UNIT,
                "h2d_bytes_per_step": int(runner.h2d_bytes), "d2h_bytes_per_step": int(runner.d2h_bytes),
                "steps": k_e2e}
 
-    # plain per-instance form (FP32 panels and matvecs, one solve call per instance), sampled
+    # plain per-instance form (FP32 panels and matvecs, one solve call per
+    # instance), on a sample spread over the size order of each kind
     plain = None
     if not args.no_plain and args.workload == "batch" and rank == 0:
-        singles = [p for p in probs if int(p.T) < 2][:3]
-        multis = [p for p in probs if int(p.T) >= 2][:1]
+        si = extremes(probs, "single", args.plain_singles)
+        mi = extremes(probs, "multi", args.plain_multis)
         ts, tm, ok = [], [], 0
-        for grp, acc in ((singles, ts), (multis, tm)):
-            for p in grp:
-                sol = api.solve(p.rounded(np.float32), precision="f32", device=str(dev), time_limit=600.0)
+        for grp, acc in ((si, ts), (mi, tm)):
+            for i in grp:
+                sol = api.solve(probs[i].rounded(np.float32), precision="f32", device=str(dev), time_limit=600.0,
+                                tol=tol_ok)
                 acc.append(sol.info["seconds"])
-                ok += int(sol.info["status"] == 0 and sol.info["rel_kkt"] <= TOL)
+                ok += int(sol.info["status"] == 0 and sol.info["rel_kkt"] <= tol_ok)
         ns = sum(1 for p in probs if int(p.T) < 2)
         nm = len(probs) - ns
         est = ns * statistics.mean(ts) + nm * statistics.mean(tm)
+        Ts = sorted({int(probs[i].T) for i in mi})
         plain = {"value": len(probs) / est, "unit": UNIT, "converged": f"{ok}/{len(ts) + len(tm)}",
-                 "sample": f"{len(ts)} single + {len(tm)} multi instances of the batch solved one call each "
-                           f"(FP32 panels, automatic cluster size); rate = {len(probs)} / "
-                           f"({ns} mean_single + {nm} mean_multi) of device seconds"}
+                 "sample": f"{len(ts)} single + {len(tm)} multi instances spread over the size order of each kind "
+                           f"(both ends included; multi T in {Ts}), solved one call each (FP32 panels, automatic "
+                           f"cluster size); rate = {len(probs)} / ({ns} mean_single + {nm} mean_multi) of device "
+                           f"seconds"}
 
+    # the other configurations, one solve each, with the oracle check
+    per_config = None
+    cfg_pending = []
+    if args.workload == "batch" and rank == 0 and not args.no_configs:
+        per_config = {}
+        for name, prob, prec in (("single n=500 k=20 FP64", S.config_single_small(), "f64"),
+                                 ("single n=10000 k=100 m=160 FP32", S.config_single_large(), "f32"),
+                                 ("multi T=20 n=5000 k=80 FP32", S.config_multi(), "f32")):
+            pr = prob if prec == "f64" else prob.rounded(np.float32)
+            sol = api.solve(pr, precision=prec, device=str(dev), return_duals=True, tol=tol_ok, time_limit=600.0)
+            per_config[name] = {"status": sol.info["status_name"], "iterations": int(sol.info["iterations"]),
+                                "device_s": float(sol.info["seconds"]), "rel_kkt": float(sol.info["rel_kkt"]),
+                                "escalated": bool(sol.info["escalated"])}
+            if pool is not None:
+                cfg_pending.append((name, pool.apply_async(_oracle_check_one,
+                                                           ((name, pr, prec, sol.x, sol.yA, sol.yD),))))
+
+    oracle_check = None
+    if pool is not None:
+        rows = [None] * len(pending)
+        for j, fut in pending:
+            rows[j] = fut.get()
+        oracle_check = summarize_check(rows)
+        oracle_check["outputs"] = ("the timed steps' outputs" if same_outputs else
+                                   "the warm-up outputs (the timed outputs differed)")
+        oracle_check["sample"] = (f"{args.check_singles} single-period and {args.check_multis} multi-period "
+                                  f"instances spread over the size order, both ends included")
+        for name, fut in cfg_pending:
+            r = fut.get()
+            per_config[name].update({"err_inf": r["err_inf"], "obj_gap": r["obj_gap"],
+                                     "oracle_rel_kkt_at_gpu_point": r.get("rel_kkt"),
+                                     "oracle_certified": r["oracle_certified"]})
+        pool.close()
+        pool.join()
+
+    # the CPU baseline is timed after the pool has finished: alone on the cores
     cpu = None
     if not args.no_cpu and rank == 0 and ws == 1 and not diff:
-        rate, sample, spent, ts, tm = oracle_sample_rate(probs, precision, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample}
+        rate, sample, spent, ts, tm = oracle_sample_rate(probs, precision)
+        cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": sample,
+               "seconds": spent}
 
     if rank == 0:
         l2_mb = torch.cuda.get_device_properties(dev).L2_cache_size / 2 ** 20
@@ -439,7 +622,10 @@ def run_ours(args):
             "dtype": {"bf16": "bf16", "f32": "f32", "f64": "f64"}[precision],
             "data": "synthetic",
             "config": {"workload": desc, "instances": len(probs), "tol": tol_ok,
-                       "precision": {"bf16": "BF16 F/A panels, FP32 matvecs, FP64 iterate state and KKT",
+                       "kkt": "relative KKT max(r_primal, r_dual, r_gap), r_gap = |P - D| / (|P| + |D|)",
+                       "precision": {"bf16": "BF16 F/A panels, FP32 matvecs, FP64 iterate state and KKT; an "
+                                             "instance that ends at the FP32 rounding floor is solved again in "
+                                             "FP64 on the same BF16-rounded data inside the step",
                                      "f32": "FP32 panels and matvecs, FP64 iterate state and KKT",
                                      "f64": "FP64 throughout"}[precision],
                        "l2": f"inputs larger than L2 ({resident_in / 2**20:.0f} MiB packed inputs, "
@@ -449,16 +635,19 @@ def run_ours(args):
                        "schedule": tuned.options() if tuned is not None else "default (cta_work 8192, check_every 64)",
                        "graph": use_graph},
             "solved": solved, "max_rel_kkt": kkt_max,
+            "escalated_fp64": max(escalated_steps, default=0),
             "iterations_mean": float(statistics.mean(iters)),
             "instance_seconds": {"sum": float(sum(inst_s)), "max": float(max(inst_s))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "team_kernel (+ the one repack launch in the same call)",
                          "peak_source": peak_src},
+            "oracle_check": oracle_check,
+            "per_config": per_config,
             "cpu_baseline": cpu,
             "plain_form": plain,
             "e2e": e2e,
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": (launches_per_step + esc_launches) * args.steps,
             "clocks": clocks,
             "step_ms": step_ms,
             "wall_s": wall,

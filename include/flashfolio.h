@@ -59,6 +59,9 @@ extern "C" {
 #define FF_TIME_LIMIT          2   /* device clock passed options.time_limit */
 #define FF_NUMERICAL           3   /* NaN/Inf met in the iteration */
 #define FF_STALLED             4   /* a bounded wait for a panel tile copy expired */
+#define FF_PRECISION           5   /* FP32/BF16 modes: the relative KKT residual stopped halving
+                                      (options.stall_checks checks): the mode's rounding floor was
+                                      reached above tol; solve again with FF_PREC_F64 */
 
 /* element types */
 #define FF_F64                 0
@@ -134,6 +137,12 @@ typedef struct ff_options {
     double  restart_artificial; /* also restart once the iterations since the last restart
                                    reach this share of all iterations so far (0 = off);
                                    default 0.36 */
+    int32_t stall_checks;       /* FP32/BF16 modes: end an instance with FF_PRECISION once its
+                                   relative KKT residual has not halved over this many checks;
+                                   0 = never; default 48 */
+    int32_t round_panels_bf16;  /* FF_PREC_F64 only: round F and A to bfloat16 (nearest even) in
+                                   the repack, so that an FP64 solve sees exactly the data of an
+                                   FF_PREC_BF16 solve of the same arrays; default 0 */
     int32_t test_expire_first_wait; /* testing aid, default 0.  1: the first wait of each
                                    instance for a panel-tile copy counts as expired (the copy
                                    itself is valid and is let land before the team moves on),
@@ -143,7 +152,8 @@ typedef struct ff_options {
 
 /* Per-instance outcome, written to DEVICE memory by the solve calls. */
 typedef struct ff_result {
-    int32_t status;             /* FF_CONVERGED, FF_MAX_ITER, FF_TIME_LIMIT, FF_NUMERICAL, FF_STALLED */
+    int32_t status;             /* FF_CONVERGED, FF_MAX_ITER, FF_TIME_LIMIT, FF_NUMERICAL, FF_STALLED,
+                                   FF_PRECISION */
     int32_t restarts;
     int64_t iterations;
     double  rel_kkt;            /* max(r_primal, r_dual, r_gap) at the returned point */
@@ -338,6 +348,38 @@ size_t ff_backward_batch_workspace_size(const ff_problem* probs, int count);
 int ff_backward_batch(const ff_problem* probs, int count, const void* const* w, const void* const* yA,
                       const void* const* yD, const void* const* grad_w, const ff_grads* out, void* ws,
                       size_t ws_bytes, int32_t* status_dev, void* stream);
+
+/* ---- risk-model estimation (Sec. 3.2) ---------------------------------
+ * For `count` estimation windows of T days (one per date; the paper uses the
+ * previous 504 business days), with p factor returns and n stock returns per
+ * day, estimate the factor model Sigma = beta Sigma_f beta^T + D of Sec. 3.2:
+ *   Sigma_f = (F - 1 1^T F / T)^T (F - 1 1^T F / T) / (T - 1),
+ *   beta_i  = least-squares coefficients of r_i ~ F beta_i (no intercept) over
+ *             the days on which stock i has a return,
+ *   D_ii    = sample variance (mean removed, divisor days - 1) of the residuals
+ *             theta_{k,i} = r_{k,i} - beta_i^T f_k over those days.
+ * A stock's returns start on its first day in the window (NaN before: a
+ * listing inside the window); a NaN after that makes it irregular.  Stocks with
+ * fewer than min_obs days (the paper: two months of history), irregular
+ * stocks, and stocks whose Gram matrix is not positive definite are not
+ * estimated: beta = 0, D = NaN.
+ *   F       : device, count x T x p float32, row k = f_k.
+ *   R       : device, count x T x n float32 (row-major: day-major), NaN = no return.
+ *   beta    : device, count x n x p float64 (output).
+ *   sigma_f : device, count x p x p float64 (output).
+ *   D       : device, count x n float64 (output).
+ *   nobs    : device, count x n int32 or NULL: days with a return, -1 irregular,
+ *             -2 singular Gram matrix (output).
+ *   ws      : device workspace of ff_risk_workspace_size bytes, 256-byte aligned.
+ * 1 <= p <= 8, 2 <= T <= 4096, n >= 1, 1 <= count <= 65535, min_obs >= 2;
+ * otherwise FF_ERR_INVALID_ARG (0 from ff_risk_workspace_size), before
+ * anything is enqueued.  Asynchronous on `stream`. */
+size_t ff_risk_workspace_size(int count, int T, int p);
+int ff_risk_estimate(int count, int T, int n, int p, const float* F, const float* R, int min_obs, double* beta,
+                     double* sigma_f, double* D, int32_t* nobs, void* ws, size_t ws_bytes, void* stream);
+/* Description of the CUDA call behind the last FF_ERR_CUDA of ff_risk_estimate
+ * on the calling host thread ("" if none). */
+const char* ff_risk_last_error(void);
 
 /* Description of the CUDA runtime call that made the last FF_ERR_CUDA return
  * on the calling host thread ("" if none); static thread-local storage. */

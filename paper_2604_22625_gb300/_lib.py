@@ -26,6 +26,7 @@ FF_MAX_ITER = 1
 FF_TIME_LIMIT = 2
 FF_NUMERICAL = 3
 FF_STALLED = 4
+FF_PRECISION = 5
 
 FF_F64 = 0
 FF_F32 = 1
@@ -37,7 +38,7 @@ FF_PREC_BF16 = 2
 FF_STATIC_WORKSPACE_BYTES = 32 * 1024 * 1024
 
 STATUS_NAMES = {FF_CONVERGED: "converged", FF_MAX_ITER: "max_iter", FF_TIME_LIMIT: "time_limit",
-                FF_NUMERICAL: "numerical", FF_STALLED: "stalled"}
+                FF_NUMERICAL: "numerical", FF_STALLED: "stalled", FF_PRECISION: "precision_floor"}
 
 
 class ff_problem(C.Structure):
@@ -56,7 +57,8 @@ class ff_options(C.Structure):
                 ("restart_sufficient", C.c_double), ("restart_necessary", C.c_double),
                 ("step_fraction", C.c_double), ("cluster_size", C.c_int32), ("max_teams", C.c_int32),
                 ("beta", C.c_double), ("reuse_workspace", C.c_int32), ("cta_work", C.c_double),
-                ("restart_artificial", C.c_double), ("test_expire_first_wait", C.c_int32)]
+                ("restart_artificial", C.c_double), ("stall_checks", C.c_int32), ("round_panels_bf16", C.c_int32),
+                ("test_expire_first_wait", C.c_int32)]
 
 
 class ff_grads(C.Structure):
@@ -82,7 +84,7 @@ EXPORTS = ("ff_default_options", "ff_workspace_size", "ff_solve_single", "ff_sol
            "ff_solve_batch", "ff_status_string", "ff_version", "ff_last_error",
            "ff_solve_single_static", "ff_batch_plan", "ff_backward", "ff_backward_single", "ff_backward_workspace_size",
            "ff_backward_batch", "ff_backward_batch_workspace_size", "ff_backward_multi_batch",
-           "ff_backward_multi_workspace_size")
+           "ff_backward_multi_workspace_size", "ff_risk_workspace_size", "ff_risk_estimate", "ff_risk_last_error")
 
 _lib = None
 
@@ -137,6 +139,14 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.ff_last_error.restype = C.c_char_p
     lib.ff_version.argtypes = []
     lib.ff_version.restype = C.c_int
+    lib.ff_risk_workspace_size.argtypes = [C.c_int, C.c_int, C.c_int]
+    lib.ff_risk_workspace_size.restype = C.c_size_t
+    lib.ff_risk_estimate.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                                     C.c_void_p]
+    lib.ff_risk_estimate.restype = C.c_int
+    lib.ff_risk_last_error.argtypes = []
+    lib.ff_risk_last_error.restype = C.c_char_p
     _lib = lib
     return lib
 
@@ -249,3 +259,18 @@ def ff_last_error() -> str:
 
 def ff_version() -> int:
     return int(load().ff_version())
+
+
+def ff_risk_workspace_size(count: int, T: int, p: int) -> int:
+    return int(load().ff_risk_workspace_size(count, T, p))
+
+
+def ff_risk_estimate(count: int, T: int, n: int, p: int, F: int, R: int, min_obs: int, beta: int, sigma_f: int,
+                     D: int, nobs: int, ws: int, ws_bytes: int, stream: int = 0) -> int:
+    return int(load().ff_risk_estimate(count, T, n, p, C.c_void_p(F), C.c_void_p(R), min_obs, C.c_void_p(beta),
+                                       C.c_void_p(sigma_f), C.c_void_p(D), C.c_void_p(nobs or None), C.c_void_p(ws),
+                                       ws_bytes, C.c_void_p(stream or None)))
+
+
+def ff_risk_last_error() -> str:
+    return load().ff_risk_last_error().decode()

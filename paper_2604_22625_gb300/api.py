@@ -91,34 +91,62 @@ def options(precision: str = "f32", **kw) -> L.ff_options:
     return L.default_options(precision=PRECISIONS[precision], **kw)
 
 
+def escalation_options(opts: L.ff_options) -> L.ff_options:
+    """Options of the FP64 re-solve of an instance that ended with
+    FF_PRECISION in the FP32 or BF16 mode: the same tolerances and limits in
+    FF_PREC_F64, with F and A rounded to bfloat16 in the repack when the first
+    solve was BF16 (so both solves see the same data)."""
+    o = L.ff_options()
+    C.pointer(o)[0] = opts
+    o.round_panels_bf16 = 1 if opts.precision == L.FF_PREC_BF16 else 0
+    o.precision = L.FF_PREC_F64
+    o.reuse_workspace = 0
+    return o
+
+
 def solve(prob, precision: str = "f32", device: str = "cuda", return_duals: bool = False,
-          stream: Optional[torch.cuda.Stream] = None, **opt_kw) -> Solution:
-    """Solve one instance on the GPU; returns host copies of the results."""
+          stream: Optional[torch.cuda.Stream] = None, escalate: bool = True, **opt_kw) -> Solution:
+    """Solve one instance on the GPU; returns host copies of the results.
+
+    With ``escalate`` (default), an FP32/BF16 solve that ends with
+    FF_PRECISION is solved again in FP64 on the same device data (the
+    returned ``info["escalated"]`` says so)."""
     dtype = torch.float64 if precision == "f64" else torch.float32
     dp = to_device(prob, dtype=dtype, device=device)
     opts = options(precision, **opt_kw)
     ws_bytes = L.ff_workspace_size(C.byref(dp.struct), 1, opts)
     if ws_bytes == 0:
         raise ValueError("invalid problem or options")
-    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=device)
     res = torch.zeros(L.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=device)
     w = torch.empty(dp.P * dp.n, dtype=dtype, device=device)
     yA = torch.empty(max(dp.P * dp.m, 1), dtype=dtype, device=device) if return_duals else None
     yD = torch.empty(dp.R * dp.n, dtype=dtype, device=device) if return_duals else None
     s = stream if stream is not None else torch.cuda.current_stream(device)
     fn = L.ff_solve_multi if dp.P > 1 or int(prob.T) >= 2 else L.ff_solve_single
-    rc = fn(dp.struct, opts, ws.data_ptr(), ws_bytes, res.data_ptr(), w.data_ptr(),
-            yA.data_ptr() if yA is not None else 0, yD.data_ptr() if yD is not None else 0, s.cuda_stream)
-    if rc != L.FF_OK:
-        raise RuntimeError(f"solve failed: {L.ff_status_string(rc)} ({rc}) {L.ff_last_error()}")
-    s.synchronize()
-    rec = res.cpu().numpy().view(L.RESULT_DTYPE)[0]
+
+    def call(o, nbytes):
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        rc = fn(dp.struct, o, ws.data_ptr(), nbytes, res.data_ptr(), w.data_ptr(),
+                yA.data_ptr() if yA is not None else 0, yD.data_ptr() if yD is not None else 0, s.cuda_stream)
+        if rc != L.FF_OK:
+            raise RuntimeError(f"solve failed: {L.ff_status_string(rc)} ({rc}) {L.ff_last_error()}")
+        s.synchronize()
+        return res.cpu().numpy().view(L.RESULT_DTYPE)[0]
+
+    rec = call(opts, ws_bytes)
+    escalated = False
+    if escalate and int(rec["status"]) == L.FF_PRECISION and opts.precision != L.FF_PREC_F64:
+        o64 = escalation_options(opts)
+        rec = call(o64, L.ff_workspace_size(C.byref(dp.struct), 1, o64))
+        escalated = True
     wn = w.cpu().numpy().astype(np.float64)
     if int(prob.T) >= 2:
         wn = wn.reshape(dp.P, dp.n)
+    info = _info(rec)
+    info["escalated"] = escalated
     return Solution(wn, yA.cpu().numpy().astype(np.float64)[:dp.P * dp.m].reshape(dp.P, dp.m) if yA is not None else None,
                     yD.cpu().numpy().astype(np.float64).reshape(dp.R, dp.n) if yD is not None else None,
-                    _info(rec))
+                    info)
 
 
 _FIELDS = ("F", "Omega", "D", "alpha", "s", "q", "w0", "wT", "A", "L", "U")
@@ -188,8 +216,11 @@ class BatchRunner:
     results back to pinned host memory, all on one stream."""
 
     def __init__(self, problems: Sequence, precision: str = "bf16", device: str = "cuda", duals: bool = False,
-                 **opt_kw):
+                 escalate: bool = True, **opt_kw):
         self.precision = precision
+        self.escalate = escalate
+        self.escalated: List[int] = []
+        self._esc_cache = {}
         self.device = torch.device(device)
         self.dtype = torch.float64 if precision == "f64" else torch.float32
         np_dtype = np.float64 if precision == "f64" else np.float32
@@ -281,9 +312,47 @@ class BatchRunner:
         with torch.cuda.stream(s):
             self.graph.replay()
 
+    def finish(self, stream: Optional[torch.cuda.Stream] = None) -> int:
+        """Wait for the solve on ``stream``; then (``escalate``) solve the
+        instances that ended with FF_PRECISION again in FP64, on the same
+        device inputs and output slots, and put their results in place.
+        Returns the number of instances solved again (``escalated`` lists them)."""
+        s = stream if stream is not None else torch.cuda.current_stream(self.device)
+        s.synchronize()
+        self.escalated = []
+        if not self.escalate or self.opts.precision == L.FF_PREC_F64:
+            return 0
+        st = self.res.view(self.count, -1)[:, :4].contiguous().view(torch.int32).cpu().numpy().ravel()
+        idx = [int(i) for i in np.nonzero(st == L.FF_PRECISION)[0]]
+        if not idx:
+            return 0
+        key = tuple(idx)
+        if key not in self._esc_cache:
+            structs = (L.ff_problem * len(idx))(*[self.structs[i] for i in idx])
+            o64 = escalation_options(self.opts)
+            nb = L.ff_workspace_size(structs, len(idx), o64)
+            if nb == 0:
+                raise ValueError("invalid problem for the FP64 re-solve")
+            ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+            res = torch.zeros(L.RESULT_DTYPE.itemsize * len(idx), dtype=torch.uint8, device=self.device)
+            self._esc_cache[key] = (structs, o64, ws, nb, res)
+        structs, o64, ws, nb, res = self._esc_cache[key]
+        def pick(v):
+            return [v[i] for i in idx]
+        rc = L.ff_solve_batch(structs, len(idx), o64, ws.data_ptr(), nb, res.data_ptr(), pick(self.w_ptrs),
+                              s.cuda_stream, pick(self.yA_ptrs) if self.yA_ptrs is not None else None,
+                              pick(self.yD_ptrs) if self.yD_ptrs is not None else None)
+        if rc != L.FF_OK:
+            raise RuntimeError(f"FP64 re-solve failed: {L.ff_status_string(rc)} ({rc}) {L.ff_last_error()}")
+        rows = torch.tensor(idx, device=self.device)
+        self.res.view(self.count, -1).index_copy_(0, rows, res.view(len(idx), -1))
+        s.synchronize()
+        self.escalated = idx
+        return len(idx)
+
     def run_from_host(self, stream: Optional[torch.cuda.Stream] = None) -> None:
-        """Copy the packed inputs from pinned host memory, solve, copy the
-        portfolios and results back (asynchronous on ``stream``)."""
+        """Copy the packed inputs from pinned host memory, solve (with the
+        FP64 re-solve of ``finish``), copy the portfolios and results back."""
         s = stream if stream is not None else torch.cuda.current_stream(self.device)
         with torch.cuda.stream(s):
             self.dev_in.copy_(self.host_in, non_blocking=True)
@@ -291,6 +360,8 @@ class BatchRunner:
                 self.graph.replay()
             else:
                 self.run(s)
+        self.finish(s)
+        with torch.cuda.stream(s):
             self.w_host.copy_(self.w_dev, non_blocking=True)
             self.res_host.copy_(self.res, non_blocking=True)
 
@@ -375,7 +446,10 @@ class BatchRunner:
 
     def results(self) -> List[dict]:
         recs = self.res.cpu().numpy().view(L.RESULT_DTYPE)
-        return [_info(r) for r in recs]
+        out = [_info(r) for r in recs]
+        for i, d in enumerate(out):
+            d["escalated"] = i in self.escalated
+        return out
 
     def portfolios(self) -> List[np.ndarray]:
         flat = self.w_dev.cpu().numpy().astype(np.float64)
@@ -390,5 +464,45 @@ def solve_batch(problems: Sequence, precision: str = "bf16", device: str = "cuda
     """Solve many instances in one persistent launch; returns (portfolios, infos)."""
     br = BatchRunner(problems, precision=precision, device=device, **opt_kw)
     br.run()
-    torch.cuda.synchronize()
+    br.finish()
     return br.portfolios(), br.results()
+
+
+@dataclass
+class RiskModels:
+    """Device results of ``estimate_risk`` for ``count`` windows."""
+    beta: torch.Tensor      # (count, n, p) float64
+    sigma_f: torch.Tensor   # (count, p, p) float64
+    D: torch.Tensor         # (count, n) float64, NaN where not estimated
+    nobs: torch.Tensor      # (count, n) int32: days with a return, -1 irregular, -2 singular
+
+
+def estimate_risk(F, R, min_obs: int = 42, device: str = "cuda",
+                  stream: Optional[torch.cuda.Stream] = None) -> RiskModels:
+    """Factor model of Sec. 3.2 for a batch of estimation windows through
+    ff_risk_estimate.  F: (count, T, p) factor returns, R: (count, T, n) stock
+    returns (NaN = no return), as arrays or tensors; stored as float32 on the
+    device."""
+    Ft = torch.as_tensor(np.asarray(F) if not torch.is_tensor(F) else F).to(device=device, dtype=torch.float32)
+    Rt = torch.as_tensor(np.asarray(R) if not torch.is_tensor(R) else R).to(device=device, dtype=torch.float32)
+    if Ft.dim() == 2:
+        Ft, Rt = Ft[None], Rt[None]
+    Ft, Rt = Ft.contiguous(), Rt.contiguous()
+    count, T, p = Ft.shape
+    n = Rt.shape[2]
+    nb = L.ff_risk_workspace_size(count, T, p)
+    if nb == 0:
+        raise ValueError("invalid sizes for the risk-model estimation")
+    ws = torch.empty(nb, dtype=torch.uint8, device=device)
+    out = RiskModels(torch.empty(count, n, p, dtype=torch.float64, device=device),
+                     torch.empty(count, p, p, dtype=torch.float64, device=device),
+                     torch.empty(count, n, dtype=torch.float64, device=device),
+                     torch.empty(count, n, dtype=torch.int32, device=device))
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    rc = L.ff_risk_estimate(count, T, n, p, Ft.data_ptr(), Rt.data_ptr(), min_obs, out.beta.data_ptr(),
+                            out.sigma_f.data_ptr(), out.D.data_ptr(), out.nobs.data_ptr(), ws.data_ptr(), nb,
+                            s.cuda_stream)
+    if rc != L.FF_OK:
+        raise RuntimeError(f"risk estimation failed: {L.ff_status_string(rc)} ({rc}) {L.ff_risk_last_error()}")
+    out._keep = (Ft, Rt, ws)
+    return out

@@ -55,20 +55,21 @@ inline Sizes sizes_of(const ff_problem& p, int precision) {
     s.R = s.multi ? p.T : 1;
     s.np = (p.n + 31) / 32 * 32;
     s.omega_diag = p.omega_diag ? 1 : 0;
-    int vcap = 0;
+    int vcap = 0, rep_glob = 0;
     const int CH = (s.P <= 64 && s.k + s.m <= 2 * kThreads)
                        ? choose_tile(s.P, s.n, s.k, s.m, s.omega_diag, matvec_elem(precision),
-                                     panel_elem(precision), &vcap)
+                                     panel_elem(precision), &vcap, &rep_glob)
                        : 0;
     s.tl = make_tiling(s.n, s.k, s.m, CH > 0 ? CH : 8);
     s.tl.CH = CH;
     s.tl.vcap = vcap;
+    s.tl.rep_glob = rep_glob;
     return s;
 }
 
 inline size_t smem_of(const Sizes& s, int precision) {
     return solver_smem_bytes(s.P, s.k, s.m, s.omega_diag, matvec_elem(precision), s.tl.CH, s.tl.Rp,
-                             panel_elem(precision), s.tl.vcap);
+                             panel_elem(precision), s.tl.vcap, s.tl.rep_glob);
 }
 
 inline size_t panel_bytes(const Sizes& s, int precision) {
@@ -91,6 +92,7 @@ size_t inst_bytes(const Sizes& s, int omega_diag, int precision) {
     b += a256((size_t)s.R * s.np * 4);                      // yDf
     b += a256((size_t)s.np * 4);                            // cenf
     b += 2 * a256((size_t)s.np * r);                        // power-iteration vectors
+    if (s.tl.rep_glob) b += a256((size_t)kMaxCluster * rep_doubles(s.P, s.k, s.m) * r);   // replicated arrays
     return b;
 }
 
@@ -149,6 +151,8 @@ void fill_defaults(ff_options* o) {
     o->cluster_size = 0;
     o->max_teams = 0;
     o->test_expire_first_wait = 0;
+    o->stall_checks = 48;
+    o->round_panels_bf16 = 0;
 }
 
 bool valid_options(const ff_options& o) {
@@ -168,6 +172,8 @@ bool valid_options(const ff_options& o) {
     if (!(o.cta_work >= 1.0)) return false;
     if (!(o.restart_artificial >= 0 && o.restart_artificial < 1)) return false;
     if (o.test_expire_first_wait != 0 && o.test_expire_first_wait != 1) return false;
+    if (o.stall_checks < 0) return false;
+    if (o.round_panels_bf16 != 0 && o.round_panels_bf16 != 1) return false;
     return true;
 }
 
@@ -183,7 +189,7 @@ template <> __device__ __forceinline__ __nv_bfloat16 to_s<__nv_bfloat16>(double 
 
 template <class In, class M, class S>
 __device__ void repack_one(const ff_problem& p, const Inst<M, S>& I, double lam2, double lam3, size_t tid,
-                           size_t nth) {
+                           size_t nth, int round_bf16) {
     const In* F = (const In*)p.F;
     const In* A = (const In*)p.A;
     const In* Om = (const In*)p.Omega;
@@ -212,6 +218,7 @@ __device__ void repack_one(const ff_problem& p, const Inst<M, S>& I, double lam2
             if (r < k) v = (double)F[(size_t)i * k + r];
             else if (r >= kp && r < kp + m) v = (double)A[(size_t)(r - kp) * n + i];
         }
+        if (round_bf16) v = (double)__bfloat162float(__float2bfloat16_rn((float)v));
         const S sv = to_s<S>(v);
         PE[e] = sv;
         PR[((size_t)t * CH + ii) * Rp + r] = sv;
@@ -248,15 +255,16 @@ __device__ void repack_one(const ff_problem& p, const Inst<M, S>& I, double lam2
 // One launch repacks every instance of the batch: blockIdx.y selects the
 // table slot, the blocks along x stride over that instance's elements.
 template <class M, class S>
-__global__ void repack_batch_kernel(const ff_problem* __restrict__ probs, const Inst<M, S>* __restrict__ insts) {
+__global__ void repack_batch_kernel(const ff_problem* __restrict__ probs, const Inst<M, S>* __restrict__ insts,
+                                    int round_bf16) {
     const ff_problem p = probs[blockIdx.y];
     const Inst<M, S> I = insts[blockIdx.y];
     const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
     const size_t nth = (size_t)gridDim.x * blockDim.x;
     if (p.dtype == FF_F64)
-        repack_one<double, M, S>(p, I, p.lambda2, p.lambda3, tid, nth);
+        repack_one<double, M, S>(p, I, p.lambda2, p.lambda3, tid, nth, round_bf16);
     else
-        repack_one<float, M, S>(p, I, p.lambda2, p.lambda3, tid, nth);
+        repack_one<float, M, S>(p, I, p.lambda2, p.lambda3, tid, nth, round_bf16);
 }
 
 template <class M, class S>
@@ -297,6 +305,8 @@ Inst<M, S> carve(const ff_problem& p, const Sizes& s, unsigned char*& cur, void*
     I.cenf = (const float*)take((size_t)s.np * 4);
     I.pv1 = (double*)take((size_t)s.np * r);
     I.pv2 = (double*)take((size_t)s.np * r);
+    I.rep_glob = s.tl.rep_glob;
+    I.rep = s.tl.rep_glob ? (double*)take((size_t)kMaxCluster * rep_doubles(s.P, s.k, s.m) * r) : nullptr;
     I.kappa = p.lambda1 * p.GMV;
     I.d = p.d;
     I.GMV = p.GMV;
@@ -387,6 +397,7 @@ Params make_params(const ff_options& o) {
     prm.beta = o.beta;
     prm.power_iters = 60;
     prm.expire_first_wait = o.test_expire_first_wait;
+    prm.stall_checks = o.stall_checks;
     prm.queue = nullptr;
     return prm;
 }
@@ -486,7 +497,8 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
     }
     if (o.reuse_workspace != 1) {
         const int bx = (int)std::min<long long>(64, (maxel + 255) / 256);
-        repack_batch_kernel<M, S><<<dim3((unsigned)bx, (unsigned)count), 256, 0, stream>>>(probs_dev, table_dev);
+        repack_batch_kernel<M, S><<<dim3((unsigned)bx, (unsigned)count), 256, 0, stream>>>(
+            probs_dev, table_dev, (o.precision == FF_PREC_F64 && o.round_panels_bf16) ? 1 : 0);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "repack launch");
     }
@@ -640,7 +652,8 @@ int run_single_static(const ff_problem& p, const ff_options& o, ff_result* res, 
     if (e != cudaSuccess) return cuda_fail(e, "record store launch");
     long long maxel = std::max((long long)sz.tl.ntile * sz.tl.Rp * sz.tl.CH, (long long)sz.np * (sz.P + sz.R));
     const int bx = (int)std::min<long long>(64, (maxel + 255) / 256);
-    repack_batch_kernel<M, S><<<dim3((unsigned)std::max(bx, 1), 1u), 256, 0, stream>>>(prob_dev, table_dev);
+    repack_batch_kernel<M, S><<<dim3((unsigned)std::max(bx, 1), 1u), 256, 0, stream>>>(
+        prob_dev, table_dev, (o.precision == FF_PREC_F64 && o.round_panels_bf16) ? 1 : 0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "repack launch");
     int* queue_dev = (int*)(base + kStage);

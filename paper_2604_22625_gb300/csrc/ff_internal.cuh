@@ -30,6 +30,7 @@ constexpr int kSmemLimit = 227 * 1024 - 4096;   // dynamic shared memory per CTA
 struct Tiling {
     int CH, kp, mp, Rp, ntile;
     int vcap;             // single period: entries of v kept in shared memory (0: v in the workspace)
+    int rep_glob;         // 1: per-period replicated arrays in the workspace (see rep_doubles)
 };
 
 __host__ __device__ inline Tiling make_tiling(int n, int k, int m, int CH) {
@@ -40,6 +41,7 @@ __host__ __device__ inline Tiling make_tiling(int n, int k, int m, int CH) {
     t.Rp = t.kp + t.mp;
     t.ntile = (n + CH - 1) / CH;
     t.vcap = 0;
+    t.rep_glob = 0;
     return t;
 }
 
@@ -52,6 +54,8 @@ struct Inst {
     int n, k, m, P, R, multi, np, omega_diag;
     int CH, kp, mp, Rp, ntile; // panel tiling (see Tiling)
     int vcap;                  // > 0: v lives in shared memory (single period)
+    int rep_glob;              // 1: yA, yAb, ax, u, ub of each CTA live in rep (workspace)
+    double* rep;               // kMaxCluster slices of rep_doubles(P, k, m) doubles, or null
     const S* PE;          // ntile tiles of [Rp][CH]
     const S* PR;          // ntile tiles of [CH][Rp]
     const double* Om;     // k x k, or k diagonal entries
@@ -93,18 +97,31 @@ struct Params {
     double beta;
     int power_iters;
     int expire_first_wait;   // test hook (ff_options.test_expire_first_wait)
+    int stall_checks;        // FP32/BF16 modes: checks without halving before FF_PRECISION (0 = off)
     int* queue;          // device counter of the next instance (zero at launch); teams take
                          // instances from it in table order
 };
 
 // Shared-memory bytes the solver kernel needs for these sizes and tiling.
 size_t solver_smem_bytes(int P, int k, int m, int omega_diag, size_t matvec_size, int CH, int Rp, size_t panel_size,
-                         int vcap);
+                         int vcap, int rep_glob);
+
+// Doubles of one CTA's slice of the replicated per-period arrays (rep_glob):
+// yA (P m), yAb (Pr m), ax (P m), u (P k), ub (Pr k), Pr = P rounded up to
+// whole chunks of kPC periods.
+__host__ __device__ inline int rep_doubles(int P, int k, int m) {
+    const int Pr = P <= 1 ? 1 : (P + kPC - 1) / kPC * kPC;
+    const int d = 2 * P * m + Pr * m + P * k + Pr * k;
+    return (d + 31) / 32 * 32;
+}
 
 // Largest tile width CH (256 down to 8) whose shared-memory layout fits, 0 if
 // none does; for a single period it first tries to keep v (n entries, FP64)
-// in shared memory as well and reports the capacity in *vcap (else 0).
-int choose_tile(int P, int n, int k, int m, int omega_diag, size_t matvec_size, size_t panel_size, int* vcap);
+// in shared memory as well and reports the capacity in *vcap (else 0); for
+// many periods it moves the replicated per-period arrays to the workspace
+// (*rep_glob = 1) when otherwise no tile of at least 32 assets fits.
+int choose_tile(int P, int n, int k, int m, int omega_diag, size_t matvec_size, size_t panel_size, int* vcap,
+                int* rep_glob);
 
 // Launch the team kernel over `count` instances (insts is a device array).
 // G = CTAs per instance (cluster size), nteams = concurrent teams; single =

@@ -71,8 +71,11 @@ struct Layout {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// rep_glob = 1: the per-period replicated arrays yA, yAb, ax, u, ub live in a
+// per-CTA slice of the workspace instead of shared memory (many periods in
+// FP64, where they would not leave room for a panel tile)
 __host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_diag, size_t ms, int CH, int Rp,
-                                              size_t ps, int vcap) {
+                                              size_t ps, int vcap, int rep_glob = 0) {
     Layout L;
     const int pct0 = P < kPC ? P : kPC;
     const int pct = pct0 <= 1 ? 1 : (pct0 <= 2 ? 2 : (pct0 <= 4 ? 4 : 8));   // template chunk width
@@ -93,13 +96,14 @@ __host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_dia
     L.sout = take((size_t)L.slen * 8);
     L.wred = take((size_t)kWarps * 32 * 8);
     L.stage = take((size_t)4 * pct * CH * (ms > 8 ? ms : 8));   // staged as M, or double at checks
-    L.yA = take((size_t)P * m * 8);
     // whole chunks for the expand pass weights (a single period needs no padding)
     const int Pr = P <= 1 ? 1 : (P + kPC - 1) / kPC * kPC;
-    L.yAb = take((size_t)Pr * m * 8);
-    L.ax = take((size_t)P * m * 8);
-    L.u = take((size_t)P * k * 8);
-    L.ub = take((size_t)Pr * k * 8);
+    const int rs = rep_glob ? 0 : 1;
+    L.yA = take((size_t)rs * P * m * 8);
+    L.yAb = take((size_t)rs * Pr * m * 8);
+    L.ax = take((size_t)rs * P * m * 8);
+    L.u = take((size_t)rs * P * k * 8);
+    L.ub = take((size_t)rs * Pr * k * 8);
     L.om = take((size_t)Pr * k * ms);
     L.yAm = take((size_t)Pr * m * ms);
     L.Om = take((size_t)(omega_diag ? k : k * k) * 8);
@@ -122,26 +126,36 @@ __host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_dia
 }
 
 size_t solver_smem_bytes(int P, int k, int m, int omega_diag, size_t matvec_size, int CH, int Rp,
-                         size_t panel_size, int vcap) {
-    return make_layout(P, k, m, omega_diag, matvec_size, CH, Rp, panel_size, vcap).total;
+                         size_t panel_size, int vcap, int rep_glob) {
+    return make_layout(P, k, m, omega_diag, matvec_size, CH, Rp, panel_size, vcap, rep_glob).total;
 }
 
-int choose_tile(int P, int n, int k, int m, int omega_diag, size_t matvec_size, size_t panel_size, int* vcap) {
+int choose_tile(int P, int n, int k, int m, int omega_diag, size_t matvec_size, size_t panel_size, int* vcap,
+                int* rep_glob) {
     const int Rp = (k + 7) / 8 * 8 + (m + 7) / 8 * 8;
     // the single-period variant is built for kSingleCtasPerSm resident CTAs
     const size_t limit = P == 1 ? (size_t)kSmemLimit / kSingleCtasPerSm - 1024 : (size_t)kSmemLimit;
     const size_t max_tile = P == 1 ? (size_t)kMaxTileBytes / kSingleCtasPerSm : (size_t)kMaxTileBytes;
-    for (int pass = (P == 1 ? 0 : 1); pass < 2; ++pass) {
+    // passes: v in shared memory (single period), everything in shared memory,
+    // per-period replicated arrays in the workspace (multi-period)
+    for (int pass = (P == 1 ? 0 : 1); pass < 3; ++pass) {
+        if (pass == 2 && P == 1) break;
+        const int rg = pass == 2 ? 1 : 0;
         for (int CH = 256; CH >= 8; CH /= 2) {
             if ((size_t)Rp * CH * panel_size > max_tile) continue;
+            // the replicated arrays move to the workspace only when the tile
+            // would otherwise be narrower than 32 assets
+            if (pass == 1 && P > 1 && CH < 32) break;
             const int vc = pass == 0 ? (n + CH - 1) / CH * CH : 0;
-            if (make_layout(P, k, m, omega_diag, matvec_size, CH, Rp, panel_size, vc).total <= limit) {
+            if (make_layout(P, k, m, omega_diag, matvec_size, CH, Rp, panel_size, vc, rg).total <= limit) {
                 *vcap = vc;
+                *rep_glob = rg;
                 return CH;
             }
         }
     }
     *vcap = 0;
+    *rep_glob = 0;
     return 0;
 }
 
@@ -1307,7 +1321,8 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         c.i1 = min(c.n, c.t1 * c.I.CH);
         const int n = c.n, k = c.k, m = c.m, P = c.P, R = c.R, np = c.np;
         const int Lr = 2 * m + 2 * k;
-        const Layout Ly = make_layout(P, k, m, c.I.omega_diag, sizeof(M), c.I.CH, c.I.Rp, sizeof(S), c.I.vcap);
+        const Layout Ly = make_layout(P, k, m, c.I.omega_diag, sizeof(M), c.I.CH, c.I.Rp, sizeof(S), c.I.vcap,
+                                      c.I.rep_glob);
         // v in shared memory holds this CTA's assets [i0, i1): offset the
         // pointer so that v[i] addresses entry i - i0
         if (PCMAX == 1 && c.I.vcap > 0) c.I.v = (double*)(smem + Ly.vbuf) - c.i0;
@@ -1324,11 +1339,22 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         c.sout = (double*)(smem + Ly.sout);
         c.wred = (double*)(smem + Ly.wred);
         c.stage = (M*)(smem + Ly.stage);
-        c.yA = (double*)(smem + Ly.yA);
-        c.yAb = (double*)(smem + Ly.yAb);
-        c.ax = (double*)(smem + Ly.ax);
-        c.u = (double*)(smem + Ly.u);
-        c.ub = (double*)(smem + Ly.ub);
+        if (c.I.rep_glob) {
+            // this CTA's slice of the workspace (no other CTA touches it)
+            const int Pr = P <= 1 ? 1 : (P + kPC - 1) / kPC * kPC;
+            double* rb = c.I.rep + (size_t)g * rep_doubles(P, k, m);
+            c.yA = rb;
+            c.yAb = c.yA + (size_t)P * m;
+            c.ax = c.yAb + (size_t)Pr * m;
+            c.u = c.ax + (size_t)P * m;
+            c.ub = c.u + (size_t)P * k;
+        } else {
+            c.yA = (double*)(smem + Ly.yA);
+            c.yAb = (double*)(smem + Ly.yAb);
+            c.ax = (double*)(smem + Ly.ax);
+            c.u = (double*)(smem + Ly.u);
+            c.ub = (double*)(smem + Ly.ub);
+        }
         c.om = (M*)(smem + Ly.om);
         c.yAm = (M*)(smem + Ly.yAm);
         c.Om = (double*)(smem + Ly.Om);
@@ -1471,6 +1497,8 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         int j = 0, restarts = 0;
         int status = FF_MAX_ITER;
         double r_restart = -1, r_prev = INFINITY, r_last = 0;
+        double stall_ref = INFINITY;   // relative KKT when it last halved
+        int stall_n = 0;               // checks since then
         double res_rel = INFINITY, res_p = 0, res_d = 0, res_g = 0, res_P = 0, res_D = 0, res_T = 0;
         for (it = 0; it < prm.max_iter; ++it) {
             const bool check = (it % prm.check_every) == 0;
@@ -1837,9 +1865,21 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             r_last = fpr;
             lap(5);
             if (sums[12] > 0) { status = FF_STALLED; break; }
-            if (!(rel == rel) || !(fpr == fpr)) { status = FF_NUMERICAL; break; }
+            // every part is tested: fmax would pass over a NaN in one of them
+            if (!(r_p == r_p) || !(r_d == r_d) || !(r_g == r_g) || !(fpr == fpr) || !(Pobj == Pobj) ||
+                !(Dobj == Dobj) || isinf(Pobj) || isinf(Dobj)) {
+                res_rel = NAN;
+                status = FF_NUMERICAL;
+                break;
+            }
             if (rel <= prm.tol) { status = FF_CONVERGED; break; }
             if (sums[11] > prm.time_limit_ns) { status = FF_TIME_LIMIT; break; }
+            // precision floor of the FP32/BF16 modes: no halving of the relative
+            // KKT residual over stall_checks checks (the rounding of the FP32
+            // products then bounds it; the host re-solves such instances in FP64)
+            if (rel <= 0.5 * stall_ref) { stall_ref = rel; stall_n = 0; }
+            else ++stall_n;
+            if (kIncr && prm.stall_checks > 0 && stall_n >= prm.stall_checks) { status = FF_PRECISION; break; }
             // restart on the fixed-point residual (sufficient / necessary decay);
             // the anchor becomes the current iterate
             if (r_restart < 0) r_restart = fpr;

@@ -245,3 +245,57 @@ def config_diff(seed: int = 4, n_single: int = 64, n_multi: int = 8) -> list:
         out.append(make_multi(50, 2000, 60, seed * 10 ** 6 + n_single + i,
                               tag="diff multi T=50 n=2000 k=60"))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Returns for the risk-model estimation of Sec. 3.2 (seeded).
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Returns:
+    """One estimation window: factor returns F (T x p) and stock returns R
+    (T x n, NaN where a stock has no return), both stored in float32 and kept
+    here as float64 copies of the float32 values.  ``beta``, ``sigma_f`` and
+    ``spec_var`` are the true parameters the data were drawn from."""
+    F: np.ndarray
+    R: np.ndarray
+    beta: np.ndarray
+    sigma_f: np.ndarray
+    spec_var: np.ndarray
+
+
+def make_returns(T: int, n: int, seed: int, p: int = 6, late_frac: float = 0.1, irregular_frac: float = 0.0,
+                 noise: bool = True) -> Returns:
+    """Daily returns from a p-factor model (the paper's market factor and five
+    Fama-French factors, p = 6): factor returns f_k ~ N(0, Sigma_f) with daily
+    volatilities U[0.4 %, 1.2 %] and random correlations; loadings: market
+    N(1, 0.3^2), the others N(0, 0.5^2); specific volatilities U[1 %, 3 %];
+    r_k = beta f_k + eps_k.  A share ``late_frac`` of the stocks start on a
+    day drawn uniformly from [1, T - 20] (NaN before: a listing inside the
+    window), a share ``irregular_frac`` has one NaN after its first return."""
+    rng = np.random.default_rng(seed)
+    vol = rng.uniform(0.004, 0.012, p)
+    Z = rng.standard_normal((p, p))
+    C = Z @ Z.T + p * np.eye(p)
+    d = np.sqrt(np.diag(C))
+    corr = C / np.outer(d, d)
+    sigma_f = corr * np.outer(vol, vol)
+    F = rng.multivariate_normal(np.zeros(p), sigma_f, size=T)
+    beta = np.empty((n, p))
+    beta[:, 0] = rng.normal(1.0, 0.3, n)
+    beta[:, 1:] = rng.normal(0.0, 0.5, (n, p - 1))
+    spec = rng.uniform(0.01, 0.03, n) ** 2
+    R = F @ beta.T
+    if noise:
+        R = R + rng.standard_normal((T, n)) * np.sqrt(spec)[None, :]
+    late = rng.uniform(0.0, 1.0, n) < late_frac
+    starts = rng.integers(1, max(2, T - 20), n)
+    for i in np.nonzero(late)[0]:
+        R[: starts[i], i] = np.nan
+    irr = np.nonzero(rng.uniform(0.0, 1.0, n) < irregular_frac)[0]
+    for i in irr:
+        first = int(np.argmax(~np.isnan(R[:, i])))
+        if first < T - 2:
+            R[rng.integers(first + 1, T), i] = np.nan
+    f32 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float32).astype(np.float64))  # noqa: E731
+    return Returns(F=f32(F), R=f32(R), beta=beta, sigma_f=sigma_f, spec_var=spec)

@@ -128,3 +128,39 @@ def test_batch_mixed_statuses(env):
     br.run()
     torch.cuda.synchronize()
     assert all(i["status"] == L.FF_CONVERGED for i in br.results())
+
+
+def test_precision_floor_then_fp64(env):
+    """FF_PRECISION: with stall_checks = 1 an FP32 solve to 1e-9 stops at the
+    first check that does not halve the relative KKT residual; the API then
+    solves the instance again in FP64 on the same device data, and the result
+    matches the oracle."""
+    torch, api = env
+    import oracle
+    prob = S.make_single(400, 10, 44, n_onehot=3).rounded(np.float32)
+    sol = api.solve(prob, precision="f32", tol=1e-9, stall_checks=1, escalate=False)
+    assert sol.info["status"] == L.FF_PRECISION, sol.info
+    sol = api.solve(prob, precision="f32", tol=1e-9, stall_checks=1)
+    assert sol.info["escalated"] and sol.info["status"] == L.FF_CONVERGED, sol.info
+    ref = oracle.solve(prob)
+    assert float(np.max(np.abs(sol.x - ref.x))) <= 1e-5
+
+
+def test_batch_bf16_precision_floor_then_fp64(env):
+    """The batched form: instances stopped by FF_PRECISION in the BF16 mode are
+    solved again in FP64 with F and A rounded to bfloat16 in the repack, so
+    they solve exactly the data of the BF16 solve (checked against the oracle
+    on the BF16-rounded data)."""
+    torch, api = env
+    import oracle
+    probs = [S.make_single(n, 16, 70 + i, n_onehot=4) for i, n in enumerate([500, 900])]
+    probs += [S.make_multi(4, 300, 8, 72, n_onehot=2)]
+    br = api.BatchRunner(probs, precision="bf16", tol=1e-9, stall_checks=1)
+    br.run()
+    assert br.finish() == len(probs)
+    infos = br.results()
+    assert all(i["status"] == L.FF_CONVERGED and i["escalated"] for i in infos), infos
+    for p, w in zip(probs, br.portfolios()):
+        pr = p.with_F_rounded_bf16()
+        ref = oracle.solve(pr)
+        assert float(np.max(np.abs(np.asarray(w).reshape(ref.x.shape) - ref.x))) <= 1e-5

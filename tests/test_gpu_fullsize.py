@@ -68,7 +68,7 @@ def test_batch_full_sampled(api):
     br = api.BatchRunner(probs, precision="bf16", tol=TOL_SOLVE)
     br.capture()
     br.replay()
-    torch.cuda.synchronize()
+    br.finish()
     infos = br.results()
     assert all(i["status_name"] == "converged" and i["rel_kkt"] <= 1e-6 for i in infos)
     ws = br.portfolios()

@@ -125,12 +125,12 @@ def test_batch_graph_replay_matches_direct_call(api):
     probs += [S.make_multi(6, 500, 40, 310)]
     br = api.BatchRunner(probs, precision="bf16", tol=TOL_SOLVE)
     br.run()
-    torch.cuda.synchronize()
+    br.finish()
     w_direct = [w.copy() for w in br.portfolios()]
     br.capture()
     br.w_dev.zero_()
     br.replay()
-    torch.cuda.synchronize()
+    br.finish()
     for a, b in zip(w_direct, br.portfolios()):
         assert np.array_equal(a, b)
     infos = br.results()
@@ -139,7 +139,7 @@ def test_batch_graph_replay_matches_direct_call(api):
     off, size = br.layout[0]["alpha"]
     br.dev_in[off:off + size] *= 0.5
     br.replay()
-    torch.cuda.synchronize()
+    br.finish()
 
     class _Sol:
         pass
@@ -156,9 +156,12 @@ def test_batch_graph_replay_matches_direct_call(api):
 def test_kernel_kkt_parts_match_oracle(api, case):
     """In FP64 mode the kernel's KKT evaluation at the returned point equals
     the oracle's (oracle/kkt.py, independent code) part by part: the
-    objective, the dual bound, r_primal, r_dual, r_gap and the term scale Phi,
-    to 1e-8 relative (the gap and the dual residual are differences of
-    nearly equal FP64 sums, so agreement beyond that is rounding order)."""
+    objective, the dual bound and the term scale Phi to 1e-12 relative;
+    r_primal, r_dual, r_gap to 1e-8 relative plus 1e-14.  The floor is the
+    rounding of the differences these ratios are made of: P - D of two FP64
+    sums of magnitude |P| carries about 1e-16 |P| of rounding, which is
+    1e-9 of r_gap at r_gap = 1e-7, and ||x - Proj(q)|| near optimality the
+    same relative to ||x||."""
     if case == "single_rows":
         prob = S.make_single(700, 14, 61, n_onehot=4)
     elif case == "single_no_rows":
@@ -179,7 +182,7 @@ def test_kernel_kkt_parts_match_oracle(api, case):
     assert close(info["primal_obj"], k.primal_obj, 1e-12), (info["primal_obj"], k.primal_obj)
     assert close(info["dual_obj"], k.dual_obj, 1e-12), (info["dual_obj"], k.dual_obj)
     assert close(info["term_scale"], k.term_scale, 1e-12), (info["term_scale"], k.term_scale)
-    assert close(info["r_gap"], k.r_gap), (info["r_gap"], k.r_gap)
-    assert close(info["r_dual"], k.r_dual), (info["r_dual"], k.r_dual)
-    assert close(info["r_primal"], k.r_primal, floor=1e-15), (info["r_primal"], k.r_primal)
-    assert close(info["rel_kkt"], k.rel_kkt), (info["rel_kkt"], k.rel_kkt)
+    assert close(info["r_gap"], k.r_gap, floor=1e-14), (info["r_gap"], k.r_gap)
+    assert close(info["r_dual"], k.r_dual, floor=1e-14), (info["r_dual"], k.r_dual)
+    assert close(info["r_primal"], k.r_primal, floor=1e-14), (info["r_primal"], k.r_primal)
+    assert close(info["rel_kkt"], k.rel_kkt, floor=1e-14), (info["rel_kkt"], k.rel_kkt)
