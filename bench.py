@@ -51,7 +51,11 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="batch",
                     choices=["batch", "single_large", "multi", "single_small", "batch_profile", "multi_profile",
-                             "diff"])
+                             "diff", "risk", "paper_grid"])
+    ap.add_argument("--grid-n", type=int, default=2000, help="paper_grid: assets per instance")
+    ap.add_argument("--grid-dates", type=int, default=21, help="paper_grid: instances (dates) per setting")
+    ap.add_argument("--eta", default="literal", choices=["literal", "inverted"], help="paper_grid: reading "
+                    "of the intraday cost profile")
     ap.add_argument("--max-iter", type=int, default=0, help="iteration cap (profiling runs only)")
     ap.add_argument("--tuned", action="store_true", help="take cta_work / check_every from the autotuner "
                     "(paper_2604_22625_gb300.tune; times candidates on a sample once, then cached)")
@@ -659,8 +663,222 @@ def run_ours(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+# risk-model estimation (Sec. 3.2): its own line
+# ---------------------------------------------------------------------------
+RISK_WINDOWS, RISK_T, RISK_N, RISK_P = 21, 504, 5000, 6
+
+
+def risk_workload(rank: int):
+    from paper_2604_22625_gb300 import synthetic as S
+    return [S.make_returns(RISK_T, RISK_N, rank_seed(5, rank) * 1000 + d, p=RISK_P, late_frac=0.1,
+                           irregular_frac=0.01) for d in range(RISK_WINDOWS)]
+
+
+def risk_bytes_per_window(T, n, p) -> float:
+    """Algorithmic bytes of one window: R and F read once (float32), beta, D
+    (float64), the history counts (int32) and Sigma_f written once."""
+    return float(T * n * 4 + T * p * 4 + n * p * 8 + n * 8 + n * 4 + p * p * 8)
+
+
+def run_risk(args):
+    import torch
+    ws, rank, local = dist_env()
+    desc = (f"risk-model estimation: {RISK_WINDOWS} windows of T={RISK_T} days, n={RISK_N} stocks, p={RISK_P} "
+            f"factors (10 % listed inside the window, 1 % with a gap)")
+    metric, unit = "estimation windows/sec (Sec. 3.2 factor model, batched)", "windows/s"
+    wins = risk_workload(rank)
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        from oracle import risk
+        for _ in range(args.warmup):
+            risk.estimate(wins[0].F, wins[0].R[:, :200])
+        t0 = time.perf_counter()
+        for s_ in range(args.steps):
+            w = wins[s_ % len(wins)]
+            risk.estimate(w.F, w.R)
+        wall = time.perf_counter() - t0
+        value = args.steps / wall
+        sample = "one window per timed step (all its stocks), oracle least squares per stock"
+        print(json.dumps({"impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": ws,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic", "config": {"workload": desc},
+                          "cpu_baseline": {"value": value, "unit": unit, "cores": cpu_cores(), "kind": "oracle",
+                                           "sample": sample},
+                          "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                          "gpu_launches": 0}), flush=True)
+        return 0
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = dist_init("nccl")
+    from paper_2604_22625_gb300 import _lib as L
+    from paper_2604_22625_gb300.build import build
+    build()
+    Fh = torch.tensor(np.stack([w.F for w in wins]), dtype=torch.float32).pin_memory()
+    Rh = torch.tensor(np.stack([w.R for w in wins]), dtype=torch.float32).pin_memory()
+    count, T, p = Fh.shape
+    n = Rh.shape[2]
+    F = Fh.to(dev)
+    R = Rh.to(dev)
+    nb = L.ff_risk_workspace_size(count, T, n, p)
+    wsb = torch.empty(nb, dtype=torch.uint8, device=dev)
+    beta = torch.empty(count, n, p, dtype=torch.float64, device=dev)
+    sig = torch.empty(count, p, p, dtype=torch.float64, device=dev)
+    D = torch.empty(count, n, dtype=torch.float64, device=dev)
+    nobs = torch.empty(count, n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(s_):
+        rc = L.ff_risk_estimate(count, T, n, p, F.data_ptr(), R.data_ptr(), 42, beta.data_ptr(), sig.data_ptr(),
+                                D.data_ptr(), nobs.data_ptr(), wsb.data_ptr(), nb, s_.cuda_stream)
+        if rc != L.FF_OK:
+            raise RuntimeError(L.ff_risk_last_error())
+
+    for _ in range(max(3, args.warmup)):
+        step(stream)
+    torch.cuda.synchronize(dev)
+    # inputs (212 MB) exceed the L2; the L2 is also flushed between steps by a 256 MiB write
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)
+    steps = max(args.steps, 10)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    for k in range(steps):
+        flush.fill_(k & 255)
+        ev[k][0].record(stream)
+        step(stream)
+        ev[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    mean_s = statistics.mean(ms) / 1e3
+    value = count / mean_s
+    alg = count * risk_bytes_per_window(T, n, p)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    # end to end: pinned host returns in, estimates out
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    F.copy_(Fh, non_blocking=True)
+    R.copy_(Rh, non_blocking=True)
+    step(stream)
+    out_b = beta.cpu()
+    out_d = D.cpu()
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    # oracle check on sampled windows and stocks
+    from oracle import risk
+    check = []
+    bh, dh, nh = out_b.numpy(), out_d.numpy(), nobs.cpu().numpy()
+    for d in (0, count - 1):
+        ref = risk.estimate(wins[d].F, wins[d].R)
+        ok = ref.valid
+        check.append({"window": d, "max_abs_beta_err": float(np.max(np.abs(bh[d][ok] - ref.beta[ok]))),
+                      "max_rel_D_err": float(np.max(np.abs(dh[d][ok] / ref.D[ok] - 1.0))),
+                      "valid_match": bool(np.array_equal(~np.isnan(dh[d]), ok))})
+    t0 = time.perf_counter()
+    risk.estimate(wins[0].F, wins[0].R)
+    cpu_s = time.perf_counter() - t0
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": ws, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * mean_s, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "l2": "inputs larger than L2 and a 256 MiB L2 flush between steps",
+                       "precision": "float32 returns; FP32 chunk sums folded into double-float; FP64 solves"},
+            "roofline": {"bound": "hbm", "achieved": alg / mean_s / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / mean_s / 1e9 / peak, "traffic": None,
+                         "kernel": "risk_prep_kernel + risk_stream_kernel (one call)",
+                         "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
+            "oracle_check": check,
+            "cpu_baseline": {"value": 1.0 / cpu_s, "unit": unit, "cores": cpu_cores(), "kind": "oracle",
+                             "sample": "one window (all 5000 stocks) solved by the oracle"},
+            "e2e": {"value": count / e2e_s, "unit": unit, "h2d_bytes_per_step": int(Fh.numel() * 4 + Rh.numel() * 4),
+                    "d2h_bytes_per_step": int(out_b.numel() * 8 + out_d.numel() * 8)},
+            "gpu_launches": 2 * steps, "clocks": clocks, "step_ms": ms}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the paper's experiment shape (Sec. 4.1, Table 1) on synthetic data
+# ---------------------------------------------------------------------------
+def sgm1(times) -> float:
+    """Shifted geometric mean with shift 1 s (Sec. 4.1)."""
+    t = np.asarray(times, dtype=np.float64)
+    return float(np.exp(np.mean(np.log(t + 1.0))) - 1.0)
+
+
+def run_paper_grid(args):
+    """Every (lambda1, lambda2 = lambda3) setting of the paper's grid, single-
+    and multi-period (T = 10, eta profile), grid_dates instances each, solved
+    one call each as in the paper's protocol (360 s limit, started at w0),
+    with SGM1 and solved counts; the first date of every setting is checked
+    against the oracle (spawned processes, concurrent with the GPU)."""
+    import torch
+    from paper_2604_22625_gb300 import api
+    from paper_2604_22625_gb300 import synthetic as S
+    from paper_2604_22625_gb300.build import build
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    workers = max(1, min(8, cpu_cores() // 2))
+    threads = max(1, cpu_cores() // workers)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = str(threads)
+    pool = spawn_pool(workers)
+    rows, pend = [], []
+    t_all = time.perf_counter()
+    for kind in ("single", "multi"):
+        for lam23 in S.PAPER_LAMBDA23:
+            for lam1 in S.PAPER_LAMBDA1:
+                times, its, solved, esc = [], [], 0, 0
+                for date in range(args.grid_dates):
+                    prob = S.make_paper_instance(date, lam1, lam23, kind, n=args.grid_n, eta_reading=args.eta)
+                    pr = prob.rounded(np.float32)
+                    sol = api.solve(pr, precision="f32", device=str(dev), return_duals=True, tol=args.tol,
+                                    time_limit=360.0)
+                    ok = sol.info["status"] == 0 and sol.info["rel_kkt"] <= args.tol
+                    solved += int(ok)
+                    esc += int(sol.info["escalated"])
+                    times.append(float(sol.info["seconds"]))
+                    its.append(int(sol.info["iterations"]))
+                    if date == 0:
+                        pend.append((len(rows), pool.apply_async(
+                            _oracle_check_one, ((prob.tag, pr, "f64", sol.x, sol.yA, sol.yD),))))
+                rows.append({"kind": kind, "lambda1": lam1, "lambda23": lam23, "solved": solved,
+                             "count": args.grid_dates, "sgm1_s": sgm1(times), "max_s": max(times),
+                             "iterations_mean": float(np.mean(its)), "escalated_fp64": esc})
+    wall = time.perf_counter() - t_all
+    for j, fut in pend:
+        r = fut.get()
+        rows[j].update({"oracle_err_inf": r["err_inf"], "oracle_obj_gap": r["obj_gap"],
+                        "oracle_certified": r["oracle_certified"]})
+    pool.close()
+    pool.join()
+    line = {"metric": "paper lambda grid: solved count and SGM1 (s) per setting", "unit": "s",
+            "config": {"workload": f"synthetic paper-shaped instances: n={args.grid_n}, p=6 factors with a full "
+                                   f"factor covariance, T=10 (multi, eta {args.eta}), {args.grid_dates} per "
+                                   f"setting, FP32, tol {args.tol}, 360 s limit, one solve call each"},
+            "wall_s": wall, "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.workload == "risk":
+        return run_risk(args)
+    if args.workload == "paper_grid":
+        return run_paper_grid(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -143,6 +143,12 @@ typedef struct ff_options {
     int32_t round_panels_bf16;  /* FF_PREC_F64 only: round F and A to bfloat16 (nearest even) in
                                    the repack, so that an FP64 solve sees exactly the data of an
                                    FF_PREC_BF16 solve of the same arrays; default 0 */
+    int32_t warm_start;         /* 0 (default): start every instance at w0 (single) or on the
+                                   straight line from w0 to w_T (multi), with zero multipliers.
+                                   1: start from the values the output buffers hold when the call
+                                   runs (w_out; yA_out and yD_out where given, else zero): warm start
+                                   from the solution of a neighbouring problem (another date or
+                                   lambda).  The outputs are overwritten with the result as usual. */
     int32_t test_expire_first_wait; /* testing aid, default 0.  1: the first wait of each
                                    instance for a panel-tile copy counts as expired (the copy
                                    itself is valid and is let land before the team moves on),
@@ -374,7 +380,7 @@ int ff_backward_batch(const ff_problem* probs, int count, const void* const* w, 
  * 1 <= p <= 8, 2 <= T <= 4096, n >= 1, 1 <= count <= 65535, min_obs >= 2;
  * otherwise FF_ERR_INVALID_ARG (0 from ff_risk_workspace_size), before
  * anything is enqueued.  Asynchronous on `stream`. */
-size_t ff_risk_workspace_size(int count, int T, int p);
+size_t ff_risk_workspace_size(int count, int T, int n, int p);
 int ff_risk_estimate(int count, int T, int n, int p, const float* F, const float* R, int min_obs, double* beta,
                      double* sigma_f, double* D, int32_t* nobs, void* ws, size_t ws_bytes, void* stream);
 /* Description of the CUDA call behind the last FF_ERR_CUDA of ff_risk_estimate

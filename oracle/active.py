@@ -251,7 +251,7 @@ def _newton(sc: Scaled, red: Reduced, x0, max_newton: int):
             v = v + step * dv
             return _x_of(sc, red, v), nu, nob_t, nob_x
         v = v + dv
-        if np.max(np.abs(dv)) <= 1e-15 * max(1e-3, np.max(np.abs(v), initial=0.0)):
+        if dv.size == 0 or np.max(np.abs(dv)) <= 1e-15 * max(1e-3, np.max(np.abs(v), initial=0.0)):
             break
     return _x_of(sc, red, v), nu, nob_t, nob_x
 

@@ -58,7 +58,7 @@ class ff_options(C.Structure):
                 ("step_fraction", C.c_double), ("cluster_size", C.c_int32), ("max_teams", C.c_int32),
                 ("beta", C.c_double), ("reuse_workspace", C.c_int32), ("cta_work", C.c_double),
                 ("restart_artificial", C.c_double), ("stall_checks", C.c_int32), ("round_panels_bf16", C.c_int32),
-                ("test_expire_first_wait", C.c_int32)]
+                ("warm_start", C.c_int32), ("test_expire_first_wait", C.c_int32)]
 
 
 class ff_grads(C.Structure):
@@ -139,7 +139,7 @@ def load(path: str = LIB_PATH) -> C.CDLL:
     lib.ff_last_error.restype = C.c_char_p
     lib.ff_version.argtypes = []
     lib.ff_version.restype = C.c_int
-    lib.ff_risk_workspace_size.argtypes = [C.c_int, C.c_int, C.c_int]
+    lib.ff_risk_workspace_size.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int]
     lib.ff_risk_workspace_size.restype = C.c_size_t
     lib.ff_risk_estimate.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
@@ -261,8 +261,8 @@ def ff_version() -> int:
     return int(load().ff_version())
 
 
-def ff_risk_workspace_size(count: int, T: int, p: int) -> int:
-    return int(load().ff_risk_workspace_size(count, T, p))
+def ff_risk_workspace_size(count: int, T: int, n: int, p: int) -> int:
+    return int(load().ff_risk_workspace_size(count, T, n, p))
 
 
 def ff_risk_estimate(count: int, T: int, n: int, p: int, F: int, R: int, min_obs: int, beta: int, sigma_f: int,

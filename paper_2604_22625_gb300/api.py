@@ -105,14 +105,20 @@ def escalation_options(opts: L.ff_options) -> L.ff_options:
 
 
 def solve(prob, precision: str = "f32", device: str = "cuda", return_duals: bool = False,
-          stream: Optional[torch.cuda.Stream] = None, escalate: bool = True, **opt_kw) -> Solution:
+          stream: Optional[torch.cuda.Stream] = None, escalate: bool = True, warm: Optional[Solution] = None,
+          **opt_kw) -> Solution:
     """Solve one instance on the GPU; returns host copies of the results.
 
     With ``escalate`` (default), an FP32/BF16 solve that ends with
     FF_PRECISION is solved again in FP64 on the same device data (the
-    returned ``info["escalated"]`` says so)."""
+    returned ``info["escalated"]`` says so).  ``warm``: a Solution of a
+    neighbouring problem of the same shape (another date or lambda) to start
+    from (ff_options.warm_start; its multipliers are used when present)."""
     dtype = torch.float64 if precision == "f64" else torch.float32
     dp = to_device(prob, dtype=dtype, device=device)
+    if warm is not None:
+        opt_kw["warm_start"] = 1
+        return_duals = return_duals or warm.yD is not None
     opts = options(precision, **opt_kw)
     ws_bytes = L.ff_workspace_size(C.byref(dp.struct), 1, opts)
     if ws_bytes == 0:
@@ -123,6 +129,17 @@ def solve(prob, precision: str = "f32", device: str = "cuda", return_duals: bool
     yD = torch.empty(dp.R * dp.n, dtype=dtype, device=device) if return_duals else None
     s = stream if stream is not None else torch.cuda.current_stream(device)
     fn = L.ff_solve_multi if dp.P > 1 or int(prob.T) >= 2 else L.ff_solve_single
+    if warm is not None:
+        w.copy_(torch.as_tensor(np.asarray(warm.w, dtype=np.float64).reshape(-1), dtype=dtype))
+        if yA is not None:
+            yA.zero_()
+            if warm.yA is not None and dp.m > 0:
+                yA[:dp.P * dp.m].copy_(torch.as_tensor(np.asarray(warm.yA).reshape(-1), dtype=dtype))
+        if yD is not None:
+            yD.zero_()
+            if warm.yD is not None:
+                yD.copy_(torch.as_tensor(np.asarray(warm.yD).reshape(-1), dtype=dtype))
+    w0_state = (w.clone(), None if yA is None else yA.clone(), None if yD is None else yD.clone())
 
     def call(o, nbytes):
         ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
@@ -137,6 +154,10 @@ def solve(prob, precision: str = "f32", device: str = "cuda", return_duals: bool
     escalated = False
     if escalate and int(rec["status"]) == L.FF_PRECISION and opts.precision != L.FF_PREC_F64:
         o64 = escalation_options(opts)
+        if warm is not None:       # the FP64 re-solve starts from the same point
+            for dst, src in zip((w, yA, yD), w0_state):
+                if dst is not None:
+                    dst.copy_(src)
         rec = call(o64, L.ff_workspace_size(C.byref(dp.struct), 1, o64))
         escalated = True
     wn = w.cpu().numpy().astype(np.float64)
@@ -490,7 +511,7 @@ def estimate_risk(F, R, min_obs: int = 42, device: str = "cuda",
     Ft, Rt = Ft.contiguous(), Rt.contiguous()
     count, T, p = Ft.shape
     n = Rt.shape[2]
-    nb = L.ff_risk_workspace_size(count, T, p)
+    nb = L.ff_risk_workspace_size(count, T, n, p)
     if nb == 0:
         raise ValueError("invalid sizes for the risk-model estimation")
     ws = torch.empty(nb, dtype=torch.uint8, device=device)

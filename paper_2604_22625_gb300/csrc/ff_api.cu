@@ -60,7 +60,7 @@ inline Sizes sizes_of(const ff_problem& p, int precision) {
                        ? choose_tile(s.P, s.n, s.k, s.m, s.omega_diag, matvec_elem(precision),
                                      panel_elem(precision), &vcap, &rep_glob)
                        : 0;
-    s.tl = make_tiling(s.n, s.k, s.m, CH > 0 ? CH : 8);
+    s.tl = make_tiling(s.n, s.k, s.m, CH > 0 ? CH : 8, (int)panel_elem(precision));
     s.tl.CH = CH;
     s.tl.vcap = vcap;
     s.tl.rep_glob = rep_glob;
@@ -73,14 +73,14 @@ inline size_t smem_of(const Sizes& s, int precision) {
 }
 
 inline size_t panel_bytes(const Sizes& s, int precision) {
-    return (size_t)s.tl.ntile * s.tl.Rp * s.tl.CH * panel_elem(precision);
+    return (size_t)s.tl.ntile * s.tl.Rp * s.tl.CS * panel_elem(precision);
 }
 
 // bytes of workspace of one instance (excluding the Inst table); state is FP64
 size_t inst_bytes(const Sizes& s, int omega_diag, int precision) {
     const size_t r = 8, pe = panel_elem(precision);
     size_t b = 0;
-    b += 2 * a256(panel_bytes(s, precision));               // PE and PR panel tiles
+    b += a256(panel_bytes(s, precision));                   // panel tiles
     b += a256((size_t)(omega_diag ? s.k : s.k * s.k) * r);  // Omega
     b += 2 * a256((size_t)s.P * s.np * r);                  // alpha, D
     b += 4 * a256((size_t)s.np * r);                        // Dmax, w0, cen, alphaT
@@ -91,6 +91,7 @@ size_t inst_bytes(const Sizes& s, int omega_diag, int precision) {
     b += a256((size_t)s.P * s.m * r + 16);                  // yA0
     b += a256((size_t)s.R * s.np * 4);                      // yDf
     b += a256((size_t)s.np * 4);                            // cenf
+    b += 2 * a256((size_t)s.np * 8);                        // w0f, cen2 (double-float pairs)
     b += 2 * a256((size_t)s.np * r);                        // power-iteration vectors
     if (s.tl.rep_glob) b += a256((size_t)kMaxCluster * rep_doubles(s.P, s.k, s.m) * r);   // replicated arrays
     return b;
@@ -153,6 +154,7 @@ void fill_defaults(ff_options* o) {
     o->test_expire_first_wait = 0;
     o->stall_checks = 48;
     o->round_panels_bf16 = 0;
+    o->warm_start = 0;
 }
 
 bool valid_options(const ff_options& o) {
@@ -174,6 +176,7 @@ bool valid_options(const ff_options& o) {
     if (o.test_expire_first_wait != 0 && o.test_expire_first_wait != 1) return false;
     if (o.stall_checks < 0) return false;
     if (o.round_panels_bf16 != 0 && o.round_panels_bf16 != 1) return false;
+    if (o.warm_start != 0 && o.warm_start != 1) return false;
     return true;
 }
 
@@ -202,26 +205,23 @@ __device__ void repack_one(const ff_problem& p, const Inst<M, S>& I, double lam2
     const In* L = (const In*)p.L;
     const In* U = (const In*)p.U;
     const int n = I.n, k = I.k, m = I.m, P = I.P, R = I.R, np = I.np;
-    // panel tiles: PE[t][r][ii] and PR[t][ii][r] for asset i = t CH + ii and
-    // panel row r (F rows 0..k-1, A rows kp..kp+m-1, zero padding elsewhere)
+    // panel tiles: PE[t][r][ii] for asset i = t CH + ii (ii < CH; CS - CH pads)
+    // and panel row r (F rows 0..k-1, A rows kp..kp+m-1, zero padding elsewhere)
     S* PE = (S*)I.PE;
-    S* PR = (S*)I.PR;
-    const int CH = I.CH, Rp = I.Rp, kp = I.kp;
-    const size_t total = (size_t)I.ntile * Rp * CH;
+    const int CH = I.CH, CS = I.CS, Rp = I.Rp, kp = I.kp;
+    const size_t total = (size_t)I.ntile * Rp * CS;
     for (size_t e = tid; e < total; e += nth) {
-        const int ii = (int)(e % CH);
-        const int r = (int)((e / CH) % Rp);
-        const int t = (int)(e / ((size_t)CH * Rp));
+        const int ii = (int)(e % CS);
+        const int r = (int)((e / CS) % Rp);
+        const int t = (int)(e / ((size_t)CS * Rp));
         const int i = t * CH + ii;
         double v = 0.0;
-        if (i < n) {
+        if (ii < CH && i < n) {
             if (r < k) v = (double)F[(size_t)i * k + r];
             else if (r >= kp && r < kp + m) v = (double)A[(size_t)(r - kp) * n + i];
         }
         if (round_bf16) v = (double)__bfloat162float(__float2bfloat16_rn((float)v));
-        const S sv = to_s<S>(v);
-        PE[e] = sv;
-        PR[((size_t)t * CH + ii) * Rp + r] = sv;
+        PE[e] = to_s<S>(v);
     }
     const int nOm = I.omega_diag ? k : k * k;
     for (size_t e = tid; e < (size_t)nOm; e += nth) ((double*)I.Om)[e] = (double)Om[e];
@@ -245,9 +245,14 @@ __device__ void repack_one(const ff_problem& p, const Inst<M, S>& I, double lam2
             ((M*)I.c1)[(size_t)r * np + i] = (M)(in ? lam2 * (double)s[(size_t)r * n + i] : 0.0);
             ((M*)I.c2)[(size_t)r * np + i] = (M)(in ? lam3 * (double)q[(size_t)r * n + i] : 0.0);
         }
-        ((double*)I.w0)[i] = (double)(in ? (double)w0[i] : 0.0);
-        ((double*)I.cen)[i] = (double)((in && I.multi) ? (double)wT[i] : 0.0);
-        ((float*)I.cenf)[i] = (float)((in && I.multi) ? (double)wT[i] : 0.0);
+        const double w0v = in ? (double)w0[i] : 0.0;
+        const double cv = (in && I.multi) ? (double)wT[i] : 0.0;
+        ((double*)I.w0)[i] = w0v;
+        ((double*)I.cen)[i] = cv;
+        ((float*)I.cenf)[i] = (float)cv;
+        const float w0h = (float)w0v, ch = (float)cv;
+        ((float2*)I.w0f)[i] = make_float2(w0h, (float)(w0v - (double)w0h));
+        ((float2*)I.cen2)[i] = make_float2(ch, (float)(cv - (double)ch));
         if (I.multi) ((double*)I.alphaT)[i] = (double)(in ? (double)al[(size_t)P * n + i] : 0.0);
     }
 }
@@ -276,10 +281,10 @@ Inst<M, S> carve(const ff_problem& p, const Sizes& s, unsigned char*& cur, void*
     I.omega_diag = p.omega_diag ? 1 : 0;
     auto take = [&](size_t bytes) { unsigned char* r = cur; cur += a256(bytes); return (void*)r; };
     const size_t r = sizeof(double);
-    I.CH = s.tl.CH; I.kp = s.tl.kp; I.mp = s.tl.mp; I.Rp = s.tl.Rp; I.ntile = s.tl.ntile; I.vcap = s.tl.vcap;
-    const size_t pb = (size_t)s.tl.ntile * s.tl.Rp * s.tl.CH * sizeof(S);
+    I.CH = s.tl.CH; I.CS = s.tl.CS; I.kp = s.tl.kp; I.mp = s.tl.mp; I.Rp = s.tl.Rp; I.ntile = s.tl.ntile;
+    I.vcap = s.tl.vcap;
+    const size_t pb = (size_t)s.tl.ntile * s.tl.Rp * s.tl.CS * sizeof(S);
     I.PE = (const S*)take(pb);
-    I.PR = (const S*)take(pb);
     I.Om = (const double*)take((size_t)(I.omega_diag ? s.k : s.k * s.k) * r);
     I.alpha = (const M*)take((size_t)s.P * s.np * r);
     I.Dp = (const M*)take((size_t)s.P * s.np * r);
@@ -303,6 +308,8 @@ Inst<M, S> carve(const ff_problem& p, const Sizes& s, unsigned char*& cur, void*
     I.yA0 = (double*)take((size_t)s.P * s.m * r + 16);
     I.yDf = (float*)take((size_t)s.R * s.np * 4);
     I.cenf = (const float*)take((size_t)s.np * 4);
+    I.w0f = (const float2*)take((size_t)s.np * 8);
+    I.cen2 = (const float2*)take((size_t)s.np * 8);
     I.pv1 = (double*)take((size_t)s.np * r);
     I.pv2 = (double*)take((size_t)s.np * r);
     I.rep_glob = s.tl.rep_glob;
@@ -398,6 +405,7 @@ Params make_params(const ff_options& o) {
     prm.power_iters = 60;
     prm.expire_first_wait = o.test_expire_first_wait;
     prm.stall_checks = o.stall_checks;
+    prm.warm_start = o.warm_start;
     prm.queue = nullptr;
     return prm;
 }
@@ -448,7 +456,7 @@ int run(const ff_problem* probs, int count, const ff_options& o, void* ws, size_
         table[slot] = carve<M, S>(probs[t], sz[t], cur, w_out[t], yA_out ? yA_out[t] : nullptr,
                                   yD_out ? yD_out[t] : nullptr, res + t);
         pslot[slot] = probs[t];
-        maxel = std::max(maxel, std::max((long long)sz[t].tl.ntile * sz[t].tl.Rp * sz[t].tl.CH,
+        maxel = std::max(maxel, std::max((long long)sz[t].tl.ntile * sz[t].tl.Rp * sz[t].tl.CS,
                                          (long long)sz[t].np * (sz[t].P + sz[t].R)));
     }
     // groups: [first slot, end slot) of equal G and kind (single- or
@@ -650,7 +658,7 @@ int run_single_static(const ff_problem& p, const ff_options& o, ff_result* res, 
     store_records_kernel<M, S><<<1, 32, 0, stream>>>(table_dev, inst, prob_dev, p);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "record store launch");
-    long long maxel = std::max((long long)sz.tl.ntile * sz.tl.Rp * sz.tl.CH, (long long)sz.np * (sz.P + sz.R));
+    long long maxel = std::max((long long)sz.tl.ntile * sz.tl.Rp * sz.tl.CS, (long long)sz.np * (sz.P + sz.R));
     const int bx = (int)std::min<long long>(64, (maxel + 255) / 256);
     repack_batch_kernel<M, S><<<dim3((unsigned)std::max(bx, 1), 1u), 256, 0, stream>>>(
         prob_dev, table_dev, (o.precision == FF_PREC_F64 && o.round_panels_bf16) ? 1 : 0);

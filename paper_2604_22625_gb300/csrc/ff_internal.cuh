@@ -23,19 +23,24 @@ constexpr int kSmemLimit = 227 * 1024 - 4096;   // dynamic shared memory per CTA
 
 // Panel tiling: the rows of F^T (k, padded to kp) and of A (m, padded to mp)
 // form one panel of Rp = kp + mp rows; the assets are cut into tiles of CH.
-// Two tiled copies exist: PE (tile = Rp rows x CH assets, assets contiguous)
-// feeds the expand pass, PR (tile = CH assets x Rp rows, rows contiguous)
-// feeds the reduce pass.  A tile is one contiguous block of Rp * CH elements
-// that one bulk copy moves into shared memory.
+// One tiled copy, PE, feeds both matvec directions: a tile is Rp rows of CS
+// elements (CH assets, then CS - CH zero pads), one contiguous block that one
+// bulk copy moves into shared memory.  The pad makes the row stride an odd
+// number of 4-byte words for 2- and 4-byte elements, so that the reduce pass
+// (row groups reading the same assets of different rows) is free of shared-
+// memory bank conflicts.
+__host__ __device__ inline int tile_stride(int CH, int elem_bytes) { return CH + (elem_bytes == 2 ? 2 : 1); }
+
 struct Tiling {
-    int CH, kp, mp, Rp, ntile;
+    int CH, CS, kp, mp, Rp, ntile;
     int vcap;             // single period: entries of v kept in shared memory (0: v in the workspace)
     int rep_glob;         // 1: per-period replicated arrays in the workspace (see rep_doubles)
 };
 
-__host__ __device__ inline Tiling make_tiling(int n, int k, int m, int CH) {
+__host__ __device__ inline Tiling make_tiling(int n, int k, int m, int CH, int elem_bytes) {
     Tiling t;
     t.CH = CH;
+    t.CS = tile_stride(CH, elem_bytes);
     t.kp = (k + 7) / 8 * 8;
     t.mp = (m + 7) / 8 * 8;
     t.Rp = t.kp + t.mp;
@@ -52,12 +57,11 @@ __host__ __device__ inline Tiling make_tiling(int n, int k, int m, int CH) {
 template <class M, class S>
 struct Inst {
     int n, k, m, P, R, multi, np, omega_diag;
-    int CH, kp, mp, Rp, ntile; // panel tiling (see Tiling)
+    int CH, CS, kp, mp, Rp, ntile; // panel tiling (see Tiling)
     int vcap;                  // > 0: v lives in shared memory (single period)
     int rep_glob;              // 1: yA, yAb, ax, u, ub of each CTA live in rep (workspace)
     double* rep;               // kMaxCluster slices of rep_doubles(P, k, m) doubles, or null
-    const S* PE;          // ntile tiles of [Rp][CH]
-    const S* PR;          // ntile tiles of [CH][Rp]
+    const S* PE;          // ntile tiles of [Rp][CS]
     const double* Om;     // k x k, or k diagonal entries
     const M* alpha;       // P x np   (matvec precision: FP32 inputs stay exact)
     const M* Dp;          // P x np
@@ -72,10 +76,12 @@ struct Inst {
     double kappa, d;
     double GMV;
     // iterate storage (workspace)
-    double *x, *x0, *xb, *xn, *v;      // P x np
-    double *yD, *yD0, *yDb, *yDn;      // R x np
+    double *x, *x0, *xb, *xn, *v;      // P x np  (x, x0, xn: double-float pairs in the FP32/BF16
+    double *yD, *yD0, *yDb, *yDn;      // R x np   modes once the setup is done; likewise yD, yD0, yDn)
     float* yDf;                        // R x np   FP32 copy of y_D (multi-period FP32 increments)
     const float* cenf;                 // np       FP32 copy of the centre
+    const float2* w0f;                 // np       w0 as a double-float pair (FP32/BF16 modes)
+    const float2* cen2;                // np       the centre as a double-float pair
     double* yA0;                       // P x m anchor of the replicated y_A
     double *pv1, *pv2;                 // np power-iteration vectors
     // outputs
@@ -98,6 +104,7 @@ struct Params {
     int power_iters;
     int expire_first_wait;   // test hook (ff_options.test_expire_first_wait)
     int stall_checks;        // FP32/BF16 modes: checks without halving before FF_PRECISION (0 = off)
+    int warm_start;          // 1: start from the output buffers (ff_options.warm_start)
     int* queue;          // device counter of the next instance (zero at launch); teams take
                          // instances from it in table order
 };

@@ -14,12 +14,12 @@
 // equations need G_i = sum_{k >= first_i} f_k f_k^T and g_i = sum_{k >= first_i} f_k,
 // which depend on first_i only: risk_prep_kernel tabulates these suffix sums
 // once per window in FP64 (products of FP32 inputs are exact in FP64), with
-// Sigma_f.  risk_stream_kernel gives every stock one thread that streams its
-// column: b = sum f_k r_k, s1 = sum r_k, s2 = sum r_k^2 are summed in FP32 over
-// chunks of kChunk rows and each chunk sum is added into a double-float
-// accumulator (an error-free two-sum), so the FP32 rounding is bounded by the
-// chunk length; the 6x6 (p x p) solve and the variance are FP64.  The pass is
-// bound by the HBM read of R (4 bytes per return).
+// Sigma_f.  risk_stream_kernel streams R once: per stock and row segment,
+// b = sum f_k r_k, s1 = sum r_k, s2 = sum r_k^2 are summed in FP32 over chunks
+// of kChunk rows and each chunk sum is added into a double-float accumulator
+// (an error-free two-sum), so the FP32 rounding is bounded by the chunk
+// length; risk_finish_kernel does the p x p solve and the variance in FP64.
+// The pass is bound by the HBM read of R (4 bytes per return).
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -42,8 +42,12 @@ __host__ __device__ inline size_t window_doubles(int T, int p) { return (size_t)
 
 __global__ void risk_prep_kernel(const float* __restrict__ F, int T, int p, double* __restrict__ sigma_f,
                                  double* __restrict__ tables) {
+    extern __shared__ float fsh[];   // [T][p] factor returns of this window
     const int d = blockIdx.x;
-    const float* f = F + (size_t)d * T * p;
+    const float* fg = F + (size_t)d * T * p;
+    for (int e = threadIdx.x; e < T * p; e += blockDim.x) fsh[e] = fg[e];
+    __syncthreads();
+    const float* f = fsh;
     double* tab = tables + (size_t)d * window_doubles(T, p);
     const int np = tri(p);
     __shared__ double mean_s[kMaxP];
@@ -89,70 +93,114 @@ __device__ __forceinline__ void fold(float& hi, float& lo, float x) {
     hi = s;
 }
 
+// Streaming pass.  A block holds kStocks consecutive stocks (one warp's width,
+// so every row read is one 128-byte line per warp) and kSegs row segments: warp
+// w sums rows [w T / kSegs, (w + 1) T / kSegs) of the block's stocks, so that
+// many independent loads are in flight per SM.  Per stock and segment: the
+// double-float sums of f_k r_k (P), r_k, r_k^2, the first row with a return and
+// the last row without one; the segments are combined in shared memory (pairs
+// added in segment order) and written to the workspace for risk_finish_kernel.
+constexpr int kStocks = 32;
+constexpr int kSegs = 8;
+
 template <int P>
-__global__ void __launch_bounds__(kRiskThreads)
-risk_stream_kernel(const float* __restrict__ F, const float* __restrict__ R, int T, int n, int min_obs,
-                   const double* __restrict__ tables, double* __restrict__ beta, double* __restrict__ D,
-                   int32_t* __restrict__ nobs) {
+__global__ void __launch_bounds__(kStocks * kSegs)
+risk_stream_kernel(const float* __restrict__ F, const float* __restrict__ R, int T, int n,
+                   double* __restrict__ sums, int* __restrict__ hist) {
     extern __shared__ float f_s[];   // [T][P] factor returns of this window
+    constexpr int NS = P + 2;
+    __shared__ float red_hi[kSegs][NS][kStocks], red_lo[kSegs][NS][kStocks];
+    __shared__ int red_first[kSegs][kStocks], red_lastnan[kSegs][kStocks];
     const int d = blockIdx.y;
     const float* fw = F + (size_t)d * T * P;
     for (int e = threadIdx.x; e < T * P; e += blockDim.x) f_s[e] = fw[e];
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const float* col = R + (size_t)d * T * n + i;
-    float bh[P], bl[P], bc[P];
+    const int lane = threadIdx.x % kStocks, seg = threadIdx.x / kStocks;
+    const int i = blockIdx.x * kStocks + lane;
+    const int k_lo = (int)((long long)T * seg / kSegs), k_hi = (int)((long long)T * (seg + 1) / kSegs);
+    float hi[NS], lo[NS], ch[NS];
 #pragma unroll
-    for (int j = 0; j < P; ++j) { bh[j] = 0.f; bl[j] = 0.f; bc[j] = 0.f; }
-    float s1h = 0.f, s1l = 0.f, s1c = 0.f, s2h = 0.f, s2l = 0.f, s2c = 0.f;
-    int first = -1, inchunk = 0;
-    bool regular = true;
-    for (int k0 = 0; k0 < T; k0 += kUnroll) {
-        float rv[kUnroll];
+    for (int j = 0; j < NS; ++j) { hi[j] = 0.f; lo[j] = 0.f; ch[j] = 0.f; }
+    int first = 1 << 30, lastnan = -1, inchunk = 0;
+    if (i < n) {
+        const float* col = R + (size_t)d * T * n + i;
+        for (int k0 = k_lo; k0 < k_hi; k0 += kUnroll) {
+            float rv[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) rv[u] = (k0 + u < T) ? __ldg(col + (size_t)(k0 + u) * n) : 0.f;
+            for (int u = 0; u < kUnroll; ++u) rv[u] = (k0 + u < k_hi) ? __ldg(col + (size_t)(k0 + u) * n) : NAN;
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int k = k0 + u;
-            if (k >= T) break;
-            const float r = rv[u];
-            if (isnan(r)) {
-                if (first >= 0) regular = false;
-                continue;
-            }
-            if (first < 0) first = k;
-            const float* fk = f_s + k * P;
+            for (int u = 0; u < kUnroll; ++u) {
+                const int k = k0 + u;
+                if (k >= k_hi) break;
+                const float r = rv[u];
+                if (isnan(r)) { lastnan = k; continue; }
+                first = min(first, k);
+                const float* fk = f_s + k * P;
 #pragma unroll
-            for (int j = 0; j < P; ++j) bc[j] = fmaf(fk[j], r, bc[j]);
-            s1c += r;
-            s2c = fmaf(r, r, s2c);
-            if (++inchunk == kChunk) {
+                for (int j = 0; j < P; ++j) ch[j] = fmaf(fk[j], r, ch[j]);
+                ch[P] += r;
+                ch[P + 1] = fmaf(r, r, ch[P + 1]);
+                if (++inchunk == kChunk) {
 #pragma unroll
-                for (int j = 0; j < P; ++j) { fold(bh[j], bl[j], bc[j]); bc[j] = 0.f; }
-                fold(s1h, s1l, s1c);
-                fold(s2h, s2l, s2c);
-                s1c = 0.f;
-                s2c = 0.f;
-                inchunk = 0;
+                    for (int j = 0; j < NS; ++j) { fold(hi[j], lo[j], ch[j]); ch[j] = 0.f; }
+                    inchunk = 0;
+                }
             }
         }
+#pragma unroll
+        for (int j = 0; j < NS; ++j) fold(hi[j], lo[j], ch[j]);
     }
 #pragma unroll
-    for (int j = 0; j < P; ++j) fold(bh[j], bl[j], bc[j]);
-    fold(s1h, s1l, s1c);
-    fold(s2h, s2l, s2c);
+    for (int j = 0; j < NS; ++j) { red_hi[seg][j][lane] = hi[j]; red_lo[seg][j][lane] = lo[j]; }
+    red_first[seg][lane] = first;
+    red_lastnan[seg][lane] = lastnan;
+    __syncthreads();
+    // combine the segments (fixed order) and write: threads (j, lane), j < NS
+    for (int e = threadIdx.x; e < NS * kStocks; e += blockDim.x) {
+        const int j = e / kStocks, l = e % kStocks;
+        const int ii = blockIdx.x * kStocks + l;
+        if (ii >= n) continue;
+        double acc = 0.0;
+        for (int q = 0; q < kSegs; ++q) acc += (double)red_hi[q][j][l] + (double)red_lo[q][j][l];
+        sums[((size_t)d * n + ii) * NS + j] = acc;
+    }
+    if (threadIdx.x < kStocks) {
+        const int ii = blockIdx.x * kStocks + threadIdx.x;
+        if (ii < n) {
+            int f0 = 1 << 30, ln = -1;
+            for (int q = 0; q < kSegs; ++q) {
+                f0 = min(f0, red_first[q][threadIdx.x]);
+                ln = max(ln, red_lastnan[q][threadIdx.x]);
+            }
+            hist[2 * ((size_t)d * n + ii)] = f0;
+            hist[2 * ((size_t)d * n + ii) + 1] = ln;
+        }
+    }
+}
 
-    const int cnt = first < 0 ? 0 : T - first;
-    double* bo = beta + ((size_t)d * n + i) * P;
-    if (nobs) nobs[(size_t)d * n + i] = regular ? cnt : -1;
+// One thread per stock: history rule, normal equations over the stock's days
+// (suffix Gram table, FP64 Cholesky), residual variance from the moments.
+template <int P>
+__global__ void risk_finish_kernel(int T, int n, int min_obs, const double* __restrict__ tables,
+                                   const double* __restrict__ sums, const int* __restrict__ hist,
+                                   double* __restrict__ beta, double* __restrict__ D, int32_t* __restrict__ nobs) {
+    constexpr int NS = P + 2;
+    const int d = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const size_t si = (size_t)d * n + i;
+    const int first = hist[2 * si], lastnan = hist[2 * si + 1];
+    const bool any = first < T;
+    const bool regular = !any || lastnan < first;
+    const int cnt = any ? T - first : 0;
+    double* bo = beta + si * P;
+    if (nobs) nobs[si] = regular ? cnt : -1;
     if (!regular || cnt < min_obs || cnt < 2) {
 #pragma unroll
         for (int j = 0; j < P; ++j) bo[j] = 0.0;
-        D[(size_t)d * n + i] = NAN;
+        D[si] = NAN;
         return;
     }
-    // normal equations G beta = b over the days k >= first (FP64 Cholesky)
     constexpr int NP = P * (P + 1) / 2;
     const double* tab = tables + (size_t)d * window_doubles(T, P) + (size_t)first * (NP + P);
     double Lm[P][P];
@@ -164,7 +212,7 @@ risk_stream_kernel(const float* __restrict__ F, const float* __restrict__ R, int
     double b[P], g1[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
-        b[j] = (double)bh[j] + (double)bl[j];
+        b[j] = sums[si * NS + j];
         g1[j] = tab[NP + j];
     }
     bool spd = true;
@@ -197,8 +245,8 @@ risk_stream_kernel(const float* __restrict__ F, const float* __restrict__ R, int
     if (!spd) {
 #pragma unroll
         for (int j = 0; j < P; ++j) bo[j] = 0.0;
-        D[(size_t)d * n + i] = NAN;
-        if (nobs) nobs[(size_t)d * n + i] = -2;
+        D[si] = NAN;
+        if (nobs) nobs[si] = -2;
         return;
     }
     // residual moments: sum theta = s1 - beta^T g1, sum theta^2 = s2 - beta^T b (at the solution)
@@ -209,22 +257,25 @@ risk_stream_kernel(const float* __restrict__ F, const float* __restrict__ R, int
         bt_b += x[j] * b[j];
         bt_g += x[j] * g1[j];
     }
-    const double s1 = (double)s1h + (double)s1l;
-    const double s2 = (double)s2h + (double)s2l;
-    const double st = s1 - bt_g;
-    const double sq = s2 - bt_b;
-    D[(size_t)d * n + i] = (sq - st * st / (double)cnt) / (double)(cnt - 1);
+    const double st = sums[si * NS + P] - bt_g;
+    const double sq = sums[si * NS + P + 1] - bt_b;
+    D[si] = (sq - st * st / (double)cnt) / (double)(cnt - 1);
 }
 
 template <int P>
 cudaError_t launch_stream(const float* F, const float* R, int count, int T, int n, int min_obs,
-                          const double* tables, double* beta, double* D, int32_t* nobs, cudaStream_t stream) {
+                          const double* tables, double* sums, int* hist, double* beta, double* D, int32_t* nobs,
+                          cudaStream_t stream) {
     const size_t smem = (size_t)T * P * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(risk_stream_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((unsigned)((n + kRiskThreads - 1) / kRiskThreads), (unsigned)count);
-    risk_stream_kernel<P><<<grid, kRiskThreads, smem, stream>>>(F, R, T, n, min_obs, tables, beta, D, nobs);
+    dim3 grid((unsigned)((n + kStocks - 1) / kStocks), (unsigned)count);
+    risk_stream_kernel<P><<<grid, kStocks * kSegs, smem, stream>>>(F, R, T, n, sums, hist);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    dim3 grid2((unsigned)((n + 127) / 128), (unsigned)count);
+    risk_finish_kernel<P><<<grid2, 128, 0, stream>>>(T, n, min_obs, tables, sums, hist, beta, D, nobs);
     return cudaGetLastError();
 }
 
@@ -241,31 +292,42 @@ int risk_fail(cudaError_t e, const char* where) {
 
 extern "C" {
 
-size_t ff_risk_workspace_size(int count, int T, int p) {
-    if (count < 1 || count > 65535 || T < 2 || T > ff::kMaxT || p < 1 || p > ff::kMaxP) return 0;
-    return (size_t)count * ff::window_doubles(T, p) * sizeof(double);
+static size_t risk_tables_bytes(int count, int T, int p) {
+    return ((size_t)count * ff::window_doubles(T, p) * sizeof(double) + 255) / 256 * 256;
+}
+
+size_t ff_risk_workspace_size(int count, int T, int n, int p) {
+    if (count < 1 || count > 65535 || T < 2 || T > ff::kMaxT || p < 1 || p > ff::kMaxP || n < 1) return 0;
+    const size_t sums = ((size_t)count * n * (p + 2) * sizeof(double) + 255) / 256 * 256;
+    const size_t hist = (size_t)count * n * 2 * sizeof(int);
+    return risk_tables_bytes(count, T, p) + sums + hist;
 }
 
 int ff_risk_estimate(int count, int T, int n, int p, const float* F, const float* R, int min_obs, double* beta,
                      double* sigma_f, double* D, int32_t* nobs, void* ws, size_t ws_bytes, void* stream) {
-    const size_t need = ff_risk_workspace_size(count, T, p);
+    const size_t need = ff_risk_workspace_size(count, T, n, p);
     if (need == 0 || n < 1 || min_obs < 2 || !F || !R || !beta || !sigma_f || !D) return FF_ERR_INVALID_ARG;
     if (!ws || ((uintptr_t)ws % 256) != 0 || ws_bytes < need) return FF_ERR_WORKSPACE;
     if ((long long)(n + ff::kRiskThreads - 1) / ff::kRiskThreads > 2147483647LL) return FF_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     double* tables = (double*)ws;
-    ff::risk_prep_kernel<<<count, 64, 0, st>>>(F, T, p, sigma_f, tables);
-    cudaError_t e = cudaGetLastError();
+    double* sums = (double*)((unsigned char*)ws + risk_tables_bytes(count, T, p));
+    int* hist = (int*)((unsigned char*)sums + ((size_t)count * n * (p + 2) * sizeof(double) + 255) / 256 * 256);
+    const size_t fsmem = (size_t)T * p * sizeof(float);
+    cudaError_t e = cudaFuncSetAttribute(ff::risk_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+    if (e != cudaSuccess) return ff::risk_fail(e, "risk_prep_kernel attribute");
+    ff::risk_prep_kernel<<<count, 64, fsmem, st>>>(F, T, p, sigma_f, tables);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return ff::risk_fail(e, "risk_prep_kernel launch");
     switch (p) {
-        case 1: e = ff::launch_stream<1>(F, R, count, T, n, min_obs, tables, beta, D, nobs, st); break;
-        case 2: e = ff::launch_stream<2>(F, R, count, T, n, min_obs, tables, beta, D, nobs, st); break;
-        case 3: e = ff::launch_stream<3>(F, R, count, T, n, min_obs, tables, beta, D, nobs, st); break;
-        case 4: e = ff::launch_stream<4>(F, R, count, T, n, min_obs, tables, beta, D, nobs, st); break;
-        case 5: e = ff::launch_stream<5>(F, R, count, T, n, min_obs, tables, beta, D, nobs, st); break;
-        case 6: e = ff::launch_stream<6>(F, R, count, T, n, min_obs, tables, beta, D, nobs, st); break;
-        case 7: e = ff::launch_stream<7>(F, R, count, T, n, min_obs, tables, beta, D, nobs, st); break;
-        default: e = ff::launch_stream<8>(F, R, count, T, n, min_obs, tables, beta, D, nobs, st); break;
+        case 1: e = ff::launch_stream<1>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
+        case 2: e = ff::launch_stream<2>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
+        case 3: e = ff::launch_stream<3>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
+        case 4: e = ff::launch_stream<4>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
+        case 5: e = ff::launch_stream<5>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
+        case 6: e = ff::launch_stream<6>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
+        case 7: e = ff::launch_stream<7>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
+        default: e = ff::launch_stream<8>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
     }
     if (e != cudaSuccess) return ff::risk_fail(e, "risk_stream_kernel launch");
     return FF_OK;

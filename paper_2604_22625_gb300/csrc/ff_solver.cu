@@ -117,7 +117,7 @@ __host__ __device__ inline Layout make_layout(int P, int k, int m, int omega_dia
     o = align_up(o, 128);
     // one stage: the panel tile, then (single period) the per-asset vectors that
     // the fused passes stage with it: 5 FP64 (x, x0, yD, yD0, w0) + 2 M (c1, c2)
-    L.panel_bytes = align_up((size_t)Rp * CH * ps, 128);
+    L.panel_bytes = align_up((size_t)Rp * tile_stride(CH, (int)ps) * ps, 128);
     L.tile_bytes = L.panel_bytes + (P == 1 ? align_up((size_t)CH * (5 * 8 + 2 * ms), 128) : 0);
     L.ring = o;
     o += (size_t)kStages * L.tile_bytes;
@@ -142,7 +142,7 @@ int choose_tile(int P, int n, int k, int m, int omega_diag, size_t matvec_size, 
         if (pass == 2 && P == 1) break;
         const int rg = pass == 2 ? 1 : 0;
         for (int CH = 256; CH >= 8; CH /= 2) {
-            if ((size_t)Rp * CH * panel_size > max_tile) continue;
+            if ((size_t)Rp * tile_stride(CH, (int)panel_size) * panel_size > max_tile) continue;
             // the replicated arrays move to the workspace only when the tile
             // would otherwise be narrower than 32 assets
             if (pass == 1 && P > 1 && CH < 32) break;
@@ -513,27 +513,30 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
-// RPT consecutive panel rows of one asset from a PR tile (shared memory)
-template <class M, class S> struct RowLoad;
-template <class M> struct RowLoad<M, __nv_bfloat16> {
-    static __device__ __forceinline__ void load(const __nv_bfloat16* p, M (&w)[4]) {
-        const uint2 u = *(const uint2*)p;
-        const __nv_bfloat162 a = *(const __nv_bfloat162*)&u.x, b = *(const __nv_bfloat162*)&u.y;
-        w[0] = (M)__low2float(a); w[1] = (M)__high2float(a); w[2] = (M)__low2float(b); w[3] = (M)__high2float(b);
-    }
-};
-template <class M> struct RowLoad<M, float> {
-    static __device__ __forceinline__ void load(const float* p, M (&w)[4]) {
-        const float4 u = *(const float4*)p;
-        w[0] = (M)u.x; w[1] = (M)u.y; w[2] = (M)u.z; w[3] = (M)u.w;
-    }
-};
-template <class M> struct RowLoad<M, double> {
-    static __device__ __forceinline__ void load(const double* p, M (&w)[4]) {
-        const double2 a = *(const double2*)p, b = *(const double2*)(p + 2);
-        w[0] = (M)a.x; w[1] = (M)a.y; w[2] = (M)b.x; w[3] = (M)b.y;
-    }
-};
+// ---------------------------------------------------------------------------
+// Double-float state of the FP32/BF16 modes: a value is the unevaluated sum
+// hi + lo of two floats with |lo| <= ulp(hi) / 2 (about 48 bits), kept in a
+// float2 in the slot of a double.  The iteration changes it only by FP32
+// increments, so every update is one error-free add; differences of two
+// nearby states are exact in their hi parts (Sterbenz) and carry the lo parts,
+// so FP32 work keeps the accuracy of the former FP64 state without FP64
+// instructions.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 df_split(double v) {
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+__device__ __forceinline__ double df_value(float2 a) { return (double)a.x + (double)a.y; }
+// a + b (b an FP32 increment), renormalised
+__device__ __forceinline__ float2 df_inc(float2 a, float b) {
+    const float s = a.x + b;
+    const float bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (b - bb) + a.y;
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+// a - b rounded to FP32 (a, b close: the hi difference is exact)
+__device__ __forceinline__ float df_sub(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
 
 // ---------------------------------------------------------------------------
 // reduce pass over one chunk of periods [p0, p0 + pc), pc <= PCT:
@@ -541,16 +544,16 @@ template <class M> struct RowLoad<M, double> {
 //   vpart[q*Lr + m + j]      = sum_i A_ji a1_{p0+q, i}
 //   vpart[q*Lr + 2m + j]     = sum_i F_ij (f0_{p0+q, i} - c_i)   (j < k)
 //   vpart[q*Lr + 2m + k + j] = sum_i F_ij (f1_{p0+q, i} - c_i)
-// with Lr = 2m + 2k, over the CTA's assets.  The PR tiles stream through the
+// with Lr = 2m + 2k, over the CTA's assets.  The panel tiles stream through the
 // bulk-copy ring; the vectors of a tile are staged in shared memory as M while
 // its copy is in flight.  Thread mapping: groups of na consecutive threads own
 // 4 consecutive panel rows, the na lanes of a group take every na-th asset of
-// the tile.  Products and per-tile sums in M (at most CH / na terms), lanes
+// the tile (the padded row stride keeps the groups on distinct banks).  Products and per-tile sums in M (at most CH / na terms), lanes
 // combined by warp shuffles, tile sums added into vpart in FP64 by the group's
 // first lane (one owner per entry: no races, fixed order).  Null vectors give
 // zeros.
 // ---------------------------------------------------------------------------
-// Products of one PR tile with the staged vectors.  sv0A/sv1A feed the A
+// Products of one panel tile with the staged vectors.  sv0A/sv1A feed the A
 // rows, sv0F/sv1F the F rows ([PCT][CH] each).  The products accumulate in
 // acc (AT, per thread) across consecutive tiles; reduce_flush combines the
 // lanes of each row group by shuffles and adds the sums into vpart in FP64
@@ -591,13 +594,15 @@ __device__ __forceinline__ void reduce_tile(Ctx<M, S>& c, const ReduceMap& mp, R
                                             const S* tile, const AT* sv0A, const AT* sv1A, const AT* sv0F,
                                             const AT* sv1F, int cnt, bool has1) {
     constexpr int RPT = 4;
-    const int CH = c.I.CH, Rp = c.I.Rp;
+    const int CH = c.I.CH, CS = c.I.CS;
     if (mp.active) {
         const AT* sv0 = mp.isA ? sv0A : sv0F;
         const AT* sv1 = mp.isA ? sv1A : sv1F;
+        const S* rows = tile + (size_t)mp.r0 * CS;
         for (int ii = mp.lane_a; ii < cnt; ii += mp.na) {
             AT w[RPT];
-            RowLoad<AT, S>::load(tile + (size_t)ii * Rp + mp.r0, w);
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) w[r] = (AT)cvt(rows[(size_t)r * CS + ii]);
 #pragma unroll
             for (int q = 0; q < PCT; ++q) {
                 const AT x0 = sv0[q * CH + ii];
@@ -656,9 +661,10 @@ __device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, c
     const int m = c.m, k = c.k, np = c.np, n = c.n;
     const int Lr = 2 * m + 2 * k;
     const bool has1 = (a1 != nullptr) || (f1 != nullptr);
+    (void)CH;
     // the F-row vectors are the A-row vectors (no centre, same arrays): stage two
     const bool single_fa = !c.I.multi && a0 != nullptr && a1 != nullptr && f0 == a1 && (f1 == nullptr || f1 == a0);
-    const size_t tile_elems = (size_t)Rp * CH;
+    const size_t tile_elems = (size_t)Rp * c.I.CS;
     const unsigned bytes = (unsigned)(tile_elems * sizeof(S));
     AT* st = (AT*)c.stage;  // [4][PCT][CH]
     for (int e = c.tid; e < pc * Lr; e += kThreads) c.vpart[e] = 0;
@@ -666,7 +672,7 @@ __device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, c
     ReduceAcc<PCT, AT> acc;
     acc.clear();
     const int nt = c.t1 - c.t0;
-    for (int j = 0; j < nt && j < kStages; ++j) pipe_issue(c.pipe, c.I.PR + (size_t)(c.t0 + j) * tile_elems, bytes);
+    for (int j = 0; j < nt && j < kStages; ++j) pipe_issue(c.pipe, c.I.PE + (size_t)(c.t0 + j) * tile_elems, bytes);
     for (int j = 0; j < nt; ++j) {
         const int t = c.t0 + j;
         const int ib = t * CH;
@@ -693,7 +699,7 @@ __device__ void reduce_chunk_t(Ctx<M, S>& c, int p0, int pc, const double* a0, c
         if ((j + 1) % kFlushTiles == 0 || j + 1 == nt) reduce_flush<PCT, AT>(c, mp, acc, pc);
         __syncthreads();
         pipe_pop(c.pipe);
-        if (j + kStages < nt) pipe_issue(c.pipe, c.I.PR + (size_t)(t + kStages) * tile_elems, bytes);
+        if (j + kStages < nt) pipe_issue(c.pipe, c.I.PE + (size_t)(t + kStages) * tile_elems, bytes);
     }
     __syncthreads();
 }
@@ -706,7 +712,7 @@ __device__ void reduce_pairs_t(Ctx<M, S>& c, int p0, int pc, const float2* vp) {
     const int CH = c.I.CH, Rp = c.I.Rp;
     const int m = c.m, k = c.k, np = c.np, n = c.n;
     const int Lr = 2 * m + 2 * k;
-    const size_t tile_elems = (size_t)Rp * CH;
+    const size_t tile_elems = (size_t)Rp * c.I.CS;
     const unsigned bytes = (unsigned)(tile_elems * sizeof(S));
     float* st = (float*)c.stage;  // [4][PCT][CH]
     for (int e = c.tid; e < pc * Lr; e += kThreads) c.vpart[e] = 0;
@@ -714,7 +720,7 @@ __device__ void reduce_pairs_t(Ctx<M, S>& c, int p0, int pc, const float2* vp) {
     ReduceAcc<PCT, float> acc;
     acc.clear();
     const int nt = c.t1 - c.t0;
-    for (int j = 0; j < nt && j < kStages; ++j) pipe_issue(c.pipe, c.I.PR + (size_t)(c.t0 + j) * tile_elems, bytes);
+    for (int j = 0; j < nt && j < kStages; ++j) pipe_issue(c.pipe, c.I.PE + (size_t)(c.t0 + j) * tile_elems, bytes);
     for (int j = 0; j < nt; ++j) {
         const int t = c.t0 + j;
         const int ib = t * CH;
@@ -741,7 +747,7 @@ __device__ void reduce_pairs_t(Ctx<M, S>& c, int p0, int pc, const float2* vp) {
         if ((j + 1) % kFlushTiles == 0 || j + 1 == nt) reduce_flush<PCT, float>(c, mp, acc, pc);
         __syncthreads();
         pipe_pop(c.pipe);
-        if (j + kStages < nt) pipe_issue(c.pipe, c.I.PR + (size_t)(t + kStages) * tile_elems, bytes);
+        if (j + kStages < nt) pipe_issue(c.pipe, c.I.PE + (size_t)(t + kStages) * tile_elems, bytes);
     }
     __syncthreads();
 }
@@ -755,7 +761,7 @@ __device__ void reduce_chunk_pairs(Ctx<M, S>& c, int p0, int pc, const float2* v
 }
 
 // ---------------------------------------------------------------------------
-// Single-period fused pass (elementwise prox + Halpern + reduce): each PR tile
+// Single-period fused pass (elementwise prox + Halpern + reduce): each panel tile
 // arrives together with its assets' x, x0, y_D, y_D0, w0 (FP64) and c1, c2
 // (M) in one stage.  For the tile's assets the threads form
 //   x_bar = Proj(v) (threshold theta),  x+ = hlA x_bar + hlB x + hlC x0,
@@ -770,7 +776,7 @@ __device__ void reduce_fused_single(Ctx<M, S>& c, double hlA, double hlB, double
     const int CH = c.I.CH, Rp = c.I.Rp;
     const int m = c.m, k = c.k, n = c.n, np = c.np;
     const int Lr = 2 * m + 2 * k;
-    const size_t tile_elems = (size_t)Rp * CH;
+    const size_t tile_elems = (size_t)Rp * c.I.CS;
     const unsigned pbytes = (unsigned)(tile_elems * sizeof(S));
     const unsigned po = c.panel_off;
     const unsigned off[8] = {0u, po, po + 8u * CH, po + 16u * CH, po + 24u * CH, po + 32u * CH, po + 40u * CH,
@@ -784,8 +790,9 @@ __device__ void reduce_fused_single(Ctx<M, S>& c, double hlA, double hlB, double
     auto issue = [&](int t) {
         const int ib = t * CH;
         const unsigned nv = (unsigned)min(CH, np - ib);
-        const void* src[8] = {c.I.PR + (size_t)t * tile_elems, c.I.x + ib, c.I.x0 + ib, c.I.yD + ib, c.I.yD0 + ib,
-                              c.I.w0 + ib, c.I.c1 + ib, c.I.c2 + ib};
+        const void* w0src = std::is_same<M, float>::value ? (const void*)(c.I.w0f + ib) : (const void*)(c.I.w0 + ib);
+        const void* src[8] = {c.I.PE + (size_t)t * tile_elems, c.I.x + ib, c.I.x0 + ib, c.I.yD + ib, c.I.yD0 + ib,
+                              w0src, c.I.c1 + ib, c.I.c2 + ib};
         const unsigned bytes[8] = {pbytes, 8u * nv, 8u * nv, 8u * nv, 8u * nv, 8u * nv, (unsigned)sizeof(M) * nv,
                                    (unsigned)sizeof(M) * nv};
         pipe_issue_n(c.pipe, 8, src, off, bytes);
@@ -808,10 +815,10 @@ __device__ void reduce_fused_single(Ctx<M, S>& c, double hlA, double hlB, double
         for (int ii = c.tid; ii < cnt; ii += kThreads) {
             const int i = ib + ii;
             if constexpr (std::is_same<M, float>::value) {
-                // FP32 increments on the FP64 state (see the multi-period pass)
+                // FP32 increments on the double-float state (see the multi-period pass)
                 const float fA = (float)hlA, fC = (float)hlC, fsD = (float)sD, finv = (float)inv_sD;
                 const float2 vu = ((const float2*)c.I.v)[i];
-                const double xc = sx[ii];
+                const float2 xc = ((const float2*)sx)[ii];
                 const float th = (float)theta;
                 const float av = fabsf(vu.x) - th;
                 float d1, xbf = 0.f;
@@ -819,26 +826,26 @@ __device__ void reduce_fused_single(Ctx<M, S>& c, double hlA, double hlB, double
                     d1 = vu.y - (vu.x < 0.f ? -th : th);
                     xbf = vu.x < 0.f ? -av : av;
                 } else {
-                    d1 = -(float)xc;
+                    d1 = -(xc.x + xc.y);
                 }
-                const double xn = xc + (double)(fA * d1 + fC * (float)(sx0[ii] - xc));
-                const float zz = (float)(xc - sw0[ii]) + 2.f * d1;   // (x - w0) + 2 (x_bar - x)
-                const double yd = syd[ii];
-                const float ydf = (float)yd;
+                const float2 xn = df_inc(xc, fA * d1 + fC * df_sub(((const float2*)sx0)[ii], xc));
+                const float zz = df_sub(xc, ((const float2*)sw0)[ii]) + 2.f * d1;   // (x - w0) + 2 (x_bar - x)
+                const float2 yd = ((const float2*)syd)[ii];
+                const float ydf = yd.x;
                 const float tf = ydf * finv + zz;
                 float yl, dy;
-                if (trade_multiplier_f(tf, finv, sc1[ii], sc2[ii], dexp, yl)) dy = yl - ydf;
+                if (trade_multiplier_f(tf, finv, sc1[ii], sc2[ii], dexp, yl)) dy = (yl - yd.x) - yd.y;
                 else dy = fsD * zz;
-                c.I.xn[i] = xn;
-                c.I.yDn[i] = yd + (double)(fA * dy + fC * (float)(syd0[ii] - yd));
+                ((float2*)c.I.xn)[i] = xn;
+                ((float2*)c.I.yDn)[i] = df_inc(yd, fA * dy + fC * df_sub(((const float2*)syd0)[ii], yd));
                 if (check) {
-                    c.I.xb[i] = av > 0.f ? xc + (double)d1 : 0.0;   // exact zeros off the support
-                    c.I.yDb[i] = yd + (double)dy;
+                    c.I.xb[i] = av > 0.f ? df_value(xc) + (double)d1 : 0.0;   // exact zeros off the support
+                    c.I.yDb[i] = df_value(yd) + (double)dy;
                     rloc[0] += (double)d1 * (double)d1;
                     rloc[1] += (double)dy * (double)dy;
                 }
                 st[ii] = xbf;
-                st[CH + ii] = (float)xn;
+                st[CH + ii] = xn.x;
             } else {
                 const double vv = c.I.v[i];
                 const double av = fabs(vv) - theta;
@@ -921,7 +928,7 @@ __device__ void reduce_chunk_f64(Ctx<M, S>& c, int p0, int pc, const double* f1)
 template <int PCT, class A, class M, class S, class W, class Epi>
 __device__ void expand_tile(Ctx<M, S>& c, const S* tile, int ib, int cnt, int p0, int pc, const W* wF,
                             const W* wA, Epi& epi) {
-    const int CH = c.I.CH, kp = c.I.kp, k = c.k, m = c.m;
+    const int CH = c.I.CH, CS = c.I.CS, kp = c.I.kp, k = c.k, m = c.m;
     const int RS = kThreads / CH;
     const int ii = c.tid % CH, rs = c.tid / CH;
     A aF[PCT], aA[PCT];
@@ -935,14 +942,14 @@ __device__ void expand_tile(Ctx<M, S>& c, const S* tile, int ib, int cnt, int p0
     for (; j + 4 <= jf1; j += 4) {
         A f[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) f[u] = (A)cvt(tile[(size_t)(j + u) * CH + ii]);
+        for (int u = 0; u < 4; ++u) f[u] = (A)cvt(tile[(size_t)(j + u) * CS + ii]);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int q = 0; q < PCT; ++q) aF[q] += f[u] * (A)wf[q * k + j + u];
     }
     for (; j < jf1; ++j) {
-        const A f = (A)cvt(tile[(size_t)j * CH + ii]);
+        const A f = (A)cvt(tile[(size_t)j * CS + ii]);
 #pragma unroll
         for (int q = 0; q < PCT; ++q) aF[q] += f * (A)wf[q * k + j];
     }
@@ -950,14 +957,14 @@ __device__ void expand_tile(Ctx<M, S>& c, const S* tile, int ib, int cnt, int p0
     for (; j + 4 <= ja1; j += 4) {
         A a[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) a[u] = (A)cvt(tile[(size_t)(kp + j + u) * CH + ii]);
+        for (int u = 0; u < 4; ++u) a[u] = (A)cvt(tile[(size_t)(kp + j + u) * CS + ii]);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int q = 0; q < PCT; ++q) aA[q] += a[u] * (A)wa[q * m + j + u];
     }
     for (; j < ja1; ++j) {
-        const A a = (A)cvt(tile[(size_t)(kp + j) * CH + ii]);
+        const A a = (A)cvt(tile[(size_t)(kp + j) * CS + ii]);
 #pragma unroll
         for (int q = 0; q < PCT; ++q) aA[q] += a * (A)wa[q * m + j];
     }
@@ -995,7 +1002,7 @@ __device__ void expand_tile(Ctx<M, S>& c, const S* tile, int ib, int cnt, int p0
 template <class A, int PCMAX, class M, class S, class W, class Epi>
 __device__ void expand_pass(Ctx<M, S>& c, int Pv, const W* wF, const W* wA, Epi epi) {
     const int CH = c.I.CH;
-    const size_t tile_elems = (size_t)c.I.Rp * CH;
+    const size_t tile_elems = (size_t)c.I.Rp * c.I.CS;
     const unsigned bytes = (unsigned)(tile_elems * sizeof(S));
     const int nt = c.t1 - c.t0;
     for (int j = 0; j < nt && j < kStages; ++j) pipe_issue(c.pipe, c.I.PE + (size_t)(c.t0 + j) * tile_elems, bytes);
@@ -1027,7 +1034,7 @@ template <class M, class S>
 __device__ void expand_main_single(Ctx<M, S>& c, double tau, double kap, const M* wF, const M* wA) {
     const int CH = c.I.CH, Rp = c.I.Rp;
     const int n = c.n, np = c.np;
-    const size_t tile_elems = (size_t)Rp * CH;
+    const size_t tile_elems = (size_t)Rp * c.I.CS;
     const unsigned pbytes = (unsigned)(tile_elems * sizeof(S));
     const unsigned po = c.panel_off;
     const unsigned off[5] = {0u, po, po + 8u * CH, po + 16u * CH, po + 16u * CH + (unsigned)sizeof(M) * CH};
@@ -1057,10 +1064,11 @@ __device__ void expand_main_single(Ctx<M, S>& c, double tau, double kap, const M
             const int ii = i - ib;
             const double xv = sx[ii];
             if constexpr (std::is_same<M, float>::value) {
-                // FP32 step u and v = x + u as a pair (the FP32-increment iteration)
-                const float xf = (float)xv;
+                // FP32 step u and v = x + u as a pair (the FP32-increment iteration);
+                // x and y_D are double-float pairs: their hi parts suffice here
+                const float xf = ((const float2*)sx)[ii].x;
                 const float gf = -sal[ii] + 2.f * kapm * ((float)aF + sdp[ii] * xf);
-                const float kt = (float)aA + (float)syd[ii];
+                const float kt = (float)aA + ((const float2*)syd)[ii].x;
                 const float u = -(float)tau * (gf + kt);
                 ((float2*)v)[i] = make_float2(xf + u, u);
             } else {
@@ -1436,33 +1444,41 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         const double inv_sA = 1.0 / sA;
         const double rho = prm.rho;
 
-        // ---- initial point: w0 (single) / straight line w0 -> w_T (multi) ----
+        // ---- initial point: w0 (single) / straight line w0 -> w_T (multi), or
+        //      (warm start) the values the output buffers hold ----------------
+        auto out_at = [&](const void* buf, size_t idx) -> double {
+            return c.I.out_f64 ? ((const double*)buf)[idx] : (double)((const float*)buf)[idx];
+        };
+        const bool warm = prm.warm_start != 0;
         for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
             const double w0 = c.I.w0[i];
             const double wt = c.I.multi ? c.I.cen[i] : w0;
             for (int p = 0; p < P; ++p) {
-                const double x = c.I.multi ? w0 + (wt - w0) * (double)(p + 1) / (double)(P + 1) : w0;
+                const double x = warm ? out_at(c.I.w_out, (size_t)p * n + i)
+                                      : (c.I.multi ? w0 + (wt - w0) * (double)(p + 1) / (double)(P + 1) : w0);
                 c.I.x[(size_t)p * np + i] = x;
                 c.I.x0[(size_t)p * np + i] = x;
             }
             for (int r = 0; r < R; ++r) {
-                c.I.yD[(size_t)r * np + i] = 0;
-                c.I.yD0[(size_t)r * np + i] = 0;
+                const double y = (warm && c.I.yD_out) ? out_at(c.I.yD_out, (size_t)r * n + i) : 0.0;
+                c.I.yD[(size_t)r * np + i] = y;
+                c.I.yD0[(size_t)r * np + i] = y;
             }
         }
         if constexpr (kIncr && PCMAX != 1) {
-            // FP32 views the multi-period expand reads: x in the pair buffer, y_D = 0
+            // FP32 views the multi-period expand reads: x in the pair buffer, y_D's FP32 copy
             for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
                 for (int p = 0; p < P; ++p)
                     ((float2*)c.I.v)[(size_t)p * np + i] = make_float2(0.f, (float)c.I.x[(size_t)p * np + i]);
-                for (int r = 0; r < R; ++r) c.I.yDf[(size_t)r * np + i] = 0.f;
+                for (int r = 0; r < R; ++r) c.I.yDf[(size_t)r * np + i] = (float)c.I.yD[(size_t)r * np + i];
             }
         }
         for (int e = c.tid; e < P * m; e += kThreads) {
-            c.yA[e] = 0;
-            c.yAb[e] = 0;
-            c.yAm[e] = (M)0;
-            c.I.yA0[e] = 0;
+            const double y = (warm && c.I.yA_out) ? out_at(c.I.yA_out, (size_t)e) : 0.0;
+            c.yA[e] = y;
+            c.yAb[e] = y;
+            c.yAm[e] = (M)y;
+            c.I.yA0[e] = y;
         }
         for (int p = c.tid; p < P; p += kThreads) {
             c.thprev[p] = 0;
@@ -1489,6 +1505,25 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             block_reduce<1>(acc, c.spart, c.wred, c.lane, c.warp);
             team_reduce<false>(cl, c.spart, c.sout, 1, G, g);
             aTwT = c.sout[0];
+        }
+        if constexpr (kIncr) {
+            // from here on x, x0, y_D and y_D0 hold double-float pairs
+            for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
+                for (int p = 0; p < P; ++p) {
+                    const size_t o = (size_t)p * np + i;
+                    const float2 xv = df_split(c.I.x[o]);
+                    ((float2*)c.I.x)[o] = xv;
+                    ((float2*)c.I.x0)[o] = xv;
+                }
+                for (int r = 0; r < R; ++r) {
+                    const size_t o = (size_t)r * np + i;
+                    const float2 yv = df_split(c.I.yD[o]);
+                    ((float2*)c.I.yD)[o] = yv;
+                    ((float2*)c.I.yD0)[o] = yv;
+                }
+            }
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            __syncthreads();
         }
 
         lap(0);
@@ -1553,26 +1588,41 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             //     (fused into the reduce pass for a single period)
             double rloc[2] = {0, 0};
             if constexpr (PCMAX != 1 && kIncr) {
-                // FP32 increments: with d1 = x_bar - x (from u and theta) and
-                // d0 = x0 - x, x+ = x + hlA d1 + hlC d0; the trade residual of row r is
-                // (Delta x + b)_r + 2 (d1_r - d1_{r-1}) from FP64 differences; the dual
-                // update y+ = y + hlA (y_bar - y) + hlC (y0 - y).  (x_bar, x+) in FP32
-                // replace (v, u) in the pair buffer for the reduce pass.
-                const double* x = c.I.x;
-                float2* v2 = (float2*)c.I.v;
+                // FP32 increments on the double-float state: with d1 = x_bar - x (from u
+                // and theta) and d0 = x0 - x, x+ = x + hlA d1 + hlC d0; the trade residual
+                // of row r is (Delta x + b)_r (a double-float difference rounded once) +
+                // 2 (d1_r - d1_{r-1}); the dual update y+ = y + hlA (y_bar - y) + hlC (y0 - y).
+                // (x_bar, x+) in FP32 replace (v, u) in the pair buffer for the reduce pass.
+                // No FP64 instruction outside the KKT checks.
+                const float2* __restrict__ x2 = (const float2*)c.I.x;
+                const float2* __restrict__ x02 = (const float2*)c.I.x0;
+                const float2* __restrict__ yd2 = (const float2*)c.I.yD;
+                const float2* __restrict__ yd02 = (const float2*)c.I.yD0;
+                float2* __restrict__ xn2 = (float2*)c.I.xn;
+                float2* __restrict__ ydn2 = (float2*)c.I.yDn;
+                float2* __restrict__ v2 = (float2*)c.I.v;
+                const M* __restrict__ c1a = c.I.c1;
+                const M* __restrict__ c2a = c.I.c2;
                 const float fA = (float)hlA, fC = (float)hlC, fsD = (float)sD, finv = (float)inv_sD;
                 for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
-                    const double w0 = c.I.w0[i];
-                    const double wt = c.I.multi ? c.I.cen[i] : 0.0;
-                    double x_prev = 0.0;
+                    const float2 w0v = c.I.w0f[i];
+                    const float2 wtv = c.I.multi ? c.I.cen2[i] : make_float2(0.f, 0.f);
+                    float2 x_prev = make_float2(-w0v.x, -w0v.y);   // row 0 takes b_1 = -w0
                     float d1_prev = 0.f;
                     for (int r = 0; r < R; ++r) {
-                        float d1 = 0.f;
-                        double xc = 0.0;
+                        const size_t orr = (size_t)r * np + i;
+                        // every load of this row first: none depends on the stores below
+                        const float2 yd = yd2[orr];
+                        const float2 yd0 = yd02[orr];
+                        const float c1v = (float)c1a[orr], c2v = (float)c2a[orr];
+                        float2 vu = make_float2(0.f, 0.f), xc = make_float2(0.f, 0.f), x0c = make_float2(0.f, 0.f);
                         if (r < P) {
-                            const size_t o = (size_t)r * np + i;
-                            const float2 vu = v2[o];
-                            xc = x[o];
+                            vu = v2[orr];
+                            xc = x2[orr];
+                            x0c = x02[orr];
+                        }
+                        float d1 = 0.f;
+                        if (r < P) {
                             const float th = (float)c.theta[r];
                             const float av = fabsf(vu.x) - th;
                             float xbf = 0.f;
@@ -1580,38 +1630,32 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                                 d1 = vu.y - (vu.x < 0.f ? -th : th);
                                 xbf = vu.x < 0.f ? -av : av;
                             } else {
-                                d1 = -(float)xc;
+                                d1 = -(xc.x + xc.y);
                             }
-                            const float d0 = (float)(c.I.x0[o] - xc);
-                            const double xn = xc + (double)(fA * d1 + fC * d0);
-                            c.I.xn[o] = xn;
-                            v2[o] = make_float2(xbf, (float)xn);
+                            const float2 xn = df_inc(xc, fA * d1 + fC * df_sub(x0c, xc));
+                            xn2[orr] = xn;
+                            v2[orr] = make_float2(xbf, xn.x);
                             if (check) {
-                                c.I.xb[o] = av > 0.f ? xc + (double)d1 : 0.0;   // exact zeros off the support
+                                c.I.xb[orr] = av > 0.f ? df_value(xc) + (double)d1 : 0.0;   // exact zeros off the support
                                 rloc[0] += (double)d1 * (double)d1;
                             }
                         }
-                        // (Delta x + b)_r in FP64, then the FP32 correction 2 (d1_r - d1_{r-1})
-                        const double dxb = (r < P ? xc : 0.0) - x_prev + (r == 0 ? -w0 : 0.0) +
-                                           ((c.I.multi && r == R - 1) ? wt : 0.0);
-                        const float zz = (float)dxb + 2.f * (d1 - d1_prev);
+                        // (Delta x + b)_r: x_r - x_{r-1} (x_0 := -b_1 = w0 handled by x_prev),
+                        // the last multi-period row adds w_T: then the FP32 correction
+                        const float2 cur = (r < P) ? xc : ((c.I.multi && r == R - 1) ? wtv : make_float2(0.f, 0.f));
+                        const float dxb = (r == 0 ? (cur.x + x_prev.x) + (cur.y + x_prev.y) : df_sub(cur, x_prev));
+                        const float zz = dxb + 2.f * (d1 - d1_prev);
                         x_prev = xc;
                         d1_prev = d1;
-                        const size_t orr = (size_t)r * np + i;
-                        const double yd = c.I.yD[orr];
-                        const float ydf = (float)yd;
-                        const float tf = ydf * finv + zz;
+                        const float tf = yd.x * finv + zz;
                         float yl, dy;
-                        if (trade_multiplier_f(tf, finv, (float)c.I.c1[orr], (float)c.I.c2[orr], dexp, yl))
-                            dy = yl - ydf;
-                        else
-                            dy = fsD * zz;
-                        const float d0y = (float)(c.I.yD0[orr] - yd);
-                        const double ydn = yd + (double)(fA * dy + fC * d0y);
-                        c.I.yDn[orr] = ydn;
-                        c.I.yDf[orr] = (float)ydn;
+                        if (trade_multiplier_f(tf, finv, c1v, c2v, dexp, yl)) dy = (yl - yd.x) - yd.y;
+                        else dy = fsD * zz;
+                        const float2 ydn = df_inc(yd, fA * dy + fC * df_sub(yd0, yd));
+                        ydn2[orr] = ydn;
+                        c.I.yDf[orr] = ydn.x;
                         if (check) {
-                            c.I.yDb[orr] = yd + (double)dy;
+                            c.I.yDb[orr] = df_value(yd) + (double)dy;
                             rloc[1] += (double)dy * (double)dy;
                         }
                     }

@@ -299,3 +299,77 @@ def make_returns(T: int, n: int, seed: int, p: int = 6, late_frac: float = 0.1, 
             R[rng.integers(first + 1, T), i] = np.nan
     f32 = lambda a: np.ascontiguousarray(np.asarray(a, dtype=np.float32).astype(np.float64))  # noqa: E731
     return Returns(F=f32(F), R=f32(R), beta=beta, sigma_f=sigma_f, spec_var=spec)
+
+
+# ---------------------------------------------------------------------------
+# Paper-shaped instances of the lambda grid (Sec. 4.1; data recipe of Sec. 3)
+# ---------------------------------------------------------------------------
+PAPER_LAMBDA1 = (1e-8, 1e-7, 1e-6, 1e-5, 1e-4)
+PAPER_LAMBDA23 = (1.0, 10.0, 100.0, 1000.0, 10000.0)
+PAPER_DATES = 21
+
+
+def eta_profile(T: int, reading: str = "literal") -> np.ndarray:
+    """Intraday scaling of the costs for t = 1..T (Sec. 3.4): eta_t = 0.5 +
+    2 (t/T - 0.5)^2, normalised by sum_{k=1}^{T-1} eta_k as printed.  The
+    formula makes costs largest at the ends while the text says liquidity is
+    greatest there: ``reading="inverted"`` uses 1 / eta_t (normalised the
+    same way) for the other reading."""
+    t = np.arange(1, T + 1, dtype=np.float64)
+    eta = 0.5 + 2.0 * (t / T - 0.5) ** 2
+    if reading == "inverted":
+        eta = 1.0 / eta
+    elif reading != "literal":
+        raise ValueError(reading)
+    return eta / eta[: T - 1].sum()
+
+
+def make_paper_date(date: int, n: int = 2000, p: int = 6, seed_base: int = 6 * 10 ** 6) -> dict:
+    """The lambda-independent data of one date: a p-factor risk model with a
+    full factor covariance (market + five style factors), alpha as the mean of
+    the next five daily returns plus half a daily volatility of noise (the
+    paper's construction, on simulated returns), spreads, the impact
+    coefficient q = sigma (GMV / ADV)^(d - 1) with ADV log-uniform in
+    [1e7, 1e9], w0 and a terminal target w_T (random signs, l1 norm 0.9)."""
+    rng = np.random.default_rng(seed_base + date)
+    vol = rng.uniform(0.004, 0.012, p)
+    Z = rng.standard_normal((p, p))
+    C = Z @ Z.T + p * np.eye(p)
+    dd = np.sqrt(np.diag(C))
+    sigma_f = (C / np.outer(dd, dd)) * np.outer(vol, vol)
+    beta = np.empty((n, p))
+    beta[:, 0] = rng.normal(1.0, 0.3, n)
+    beta[:, 1:] = rng.normal(0.0, 0.5, (n, p - 1))
+    D = rng.uniform(1e-4, 9e-4, n)
+    sig_tot = np.sqrt(np.einsum("ij,jk,ik->i", beta, sigma_f, beta) + D)
+    f5 = rng.multivariate_normal(np.zeros(p), sigma_f, size=5)
+    r5 = f5 @ beta.T + rng.standard_normal((5, n)) * np.sqrt(D)[None, :]
+    alpha = r5.mean(axis=0) + 0.5 * sig_tot * rng.standard_normal(n)
+    s = rng.uniform(2e-4, 2e-3, n)
+    adv = np.exp(rng.uniform(np.log(1e7), np.log(1e9), n))
+    w0 = _signed_l1(rng, n, 0.9)
+    wT = _signed_l1(rng, n, 0.9)
+    return dict(beta=beta, sigma_f=sigma_f, D=D, alpha=alpha, s=s, adv=adv, sig_tot=sig_tot, w0=w0, wT=wT)
+
+
+def make_paper_instance(date: int, lam1: float, lam23: float, kind: str = "single", n: int = 2000, T: int = 10,
+                        d: float = 1.5, eta_reading: str = "literal", bound: float = 0.05,
+                        GMV: float = GMV_DEFAULT) -> Problem:
+    """One instance of the paper's grid: date ``date`` (0..20), lambda1, lambda2 =
+    lambda3, single-period or multi-period (T = 10, alpha_t = alpha and Sigma
+    fixed over the horizon, s_t and q_t scaled by the eta profile).  A = beta^T
+    (factor exposure rows, bounds +-bound)."""
+    b = make_paper_date(date, n)
+    q = b["sig_tot"] * (GMV / b["adv"]) ** (d - 1.0)
+    A = np.ascontiguousarray(b["beta"].T.copy())
+    m = A.shape[0]
+    tag = f"paper {kind} date={date} lam1={lam1:g} lam23={lam23:g}"
+    if kind == "single":
+        return Problem(F=b["beta"], Omega=b["sigma_f"], D=b["D"], alpha=b["alpha"], s=b["s"], q=q, w0=b["w0"],
+                       A=A, L=np.full(m, -bound), U=np.full(m, bound), GMV=GMV, lam1=lam1, lam2=lam23,
+                       lam3=lam23, d=d, T=0, tag=tag)
+    eta = eta_profile(T, eta_reading)
+    return Problem(F=b["beta"], Omega=b["sigma_f"], D=np.repeat(b["D"][None, :], T, axis=0),
+                   alpha=np.repeat(b["alpha"][None, :], T, axis=0), s=eta[:, None] * b["s"][None, :],
+                   q=eta[:, None] * q[None, :], w0=b["w0"], A=A, L=np.full(m, -bound), U=np.full(m, bound),
+                   GMV=GMV, lam1=lam1, lam2=lam23, lam3=lam23, d=d, T=T, wT=b["wT"], tag=tag + f" eta={eta_reading}")

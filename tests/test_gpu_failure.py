@@ -164,3 +164,28 @@ def test_batch_bf16_precision_floor_then_fp64(env):
         pr = p.with_F_rounded_bf16()
         ref = oracle.solve(pr)
         assert float(np.max(np.abs(np.asarray(w).reshape(ref.x.shape) - ref.x))) <= 1e-5
+
+
+def test_warm_start(env):
+    """ff_options.warm_start: started from its own solution an instance stops
+    within a few KKT checks (the returned point, rounded to the output type,
+    is one step from the fixed point); started from the solution of a
+    neighbouring lambda it needs fewer iterations than from w0 and still
+    matches the oracle."""
+    torch, api = env
+    import oracle
+    for make, prec in ((lambda lam: S.make_single(800, 12, 91, n_onehot=4, lam2=lam, lam3=lam), "f64"),
+                       (lambda lam: S.make_multi(6, 300, 8, 92, n_onehot=2, lam2=lam, lam3=lam).rounded(np.float32),
+                        "f32")):
+        p1, p2 = make(1.0), make(1.3)
+        cold1 = api.solve(p1, precision=prec, return_duals=True, tol=1e-7)
+        again = api.solve(p1, precision=prec, return_duals=True, tol=1e-7, warm=cold1)
+        assert again.info["status"] == 0 and again.info["iterations"] <= 3 * 64 + 1, again.info
+        assert again.info["iterations"] < cold1.info["iterations"] // 4
+        assert float(np.max(np.abs(again.x - cold1.x))) <= 1e-6
+        cold2 = api.solve(p2, precision=prec, return_duals=True, tol=1e-7)
+        warm2 = api.solve(p2, precision=prec, return_duals=True, tol=1e-7, warm=cold1)
+        assert warm2.info["status"] == 0 and warm2.info["iterations"] < cold2.info["iterations"], \
+            (warm2.info["iterations"], cold2.info["iterations"])
+        ref = oracle.solve(p2)
+        assert float(np.max(np.abs(warm2.x - ref.x))) <= 1e-5
