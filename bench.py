@@ -56,6 +56,8 @@ def parse_args(argv=None):
     ap.add_argument("--grid-dates", type=int, default=21, help="paper_grid: instances (dates) per setting")
     ap.add_argument("--eta", default="literal", choices=["literal", "inverted"], help="paper_grid: reading "
                     "of the intraday cost profile")
+    ap.add_argument("--primal-weight", type=int, default=-1, help="1/0: adaptive primal weight on/off "
+                    "(-1: the library default)")
     ap.add_argument("--max-iter", type=int, default=0, help="iteration cap (profiling runs only)")
     ap.add_argument("--tuned", action="store_true", help="take cta_work / check_every from the autotuner "
                     "(paper_2604_22625_gb300.tune; times candidates on a sample once, then cached)")
@@ -836,6 +838,7 @@ def run_paper_grid(args):
         os.environ[v] = str(threads)
     pool = spawn_pool(workers)
     rows, pend = [], []
+    grid_kw = {} if args.primal_weight < 0 else {"primal_weight": args.primal_weight}
     t_all = time.perf_counter()
     for kind in ("single", "multi"):
         for lam23 in S.PAPER_LAMBDA23:
@@ -845,11 +848,12 @@ def run_paper_grid(args):
                     prob = S.make_paper_instance(date, lam1, lam23, kind, n=args.grid_n, eta_reading=args.eta)
                     pr = prob.rounded(np.float32)
                     sol = api.solve(pr, precision="f32", device=str(dev), return_duals=True, tol=args.tol,
-                                    time_limit=360.0)
+                                    time_limit=360.0, **grid_kw)
                     ok = sol.info["status"] == 0 and sol.info["rel_kkt"] <= args.tol
                     solved += int(ok)
                     esc += int(sol.info["escalated"])
-                    times.append(float(sol.info["seconds"]))
+                    # an escalated solve's time includes the FP32 attempt
+                    times.append(float(sol.info["seconds"]) + float(sol.info.get("first_seconds", 0.0)))
                     its.append(int(sol.info["iterations"]))
                     if date == 0:
                         pend.append((len(rows), pool.apply_async(

@@ -149,6 +149,14 @@ typedef struct ff_options {
                                    runs (w_out; yA_out and yD_out where given, else zero): warm start
                                    from the solution of a neighbouring problem (another date or
                                    lambda).  The outputs are overwritten with the result as usual. */
+    int32_t panel_l2_keep;      /* 1 (default): the copies of the panel tiles ask the L2 to keep
+                                   their lines (evict_last policy); every iteration reads an
+                                   instance's panel twice.  0: default L2 policy */
+    int32_t primal_weight;      /* 0 (default): fixed steps.  1: adaptive primal weight: at every
+                                   restart the ratio of the dual to the primal step moves halfway (in
+                                   logarithm) toward the ratio of the distances the dual and the
+                                   primal iterates travelled since the previous restart; the steps
+                                   keep satisfying the Condat-Vu condition */
     int32_t test_expire_first_wait; /* testing aid, default 0.  1: the first wait of each
                                    instance for a panel-tile copy counts as expired (the copy
                                    itself is valid and is let land before the team moves on),

@@ -58,7 +58,8 @@ class ff_options(C.Structure):
                 ("step_fraction", C.c_double), ("cluster_size", C.c_int32), ("max_teams", C.c_int32),
                 ("beta", C.c_double), ("reuse_workspace", C.c_int32), ("cta_work", C.c_double),
                 ("restart_artificial", C.c_double), ("stall_checks", C.c_int32), ("round_panels_bf16", C.c_int32),
-                ("warm_start", C.c_int32), ("test_expire_first_wait", C.c_int32)]
+                ("warm_start", C.c_int32), ("panel_l2_keep", C.c_int32), ("primal_weight", C.c_int32),
+                ("test_expire_first_wait", C.c_int32)]
 
 
 class ff_grads(C.Structure):

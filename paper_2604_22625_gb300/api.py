@@ -152,7 +152,9 @@ def solve(prob, precision: str = "f32", device: str = "cuda", return_duals: bool
 
     rec = call(opts, ws_bytes)
     escalated = False
+    first_seconds = 0.0
     if escalate and int(rec["status"]) == L.FF_PRECISION and opts.precision != L.FF_PREC_F64:
+        first_seconds = float(rec["seconds"])
         o64 = escalation_options(opts)
         if warm is not None:       # the FP64 re-solve starts from the same point
             for dst, src in zip((w, yA, yD), w0_state):
@@ -165,6 +167,7 @@ def solve(prob, precision: str = "f32", device: str = "cuda", return_duals: bool
         wn = wn.reshape(dp.P, dp.n)
     info = _info(rec)
     info["escalated"] = escalated
+    info["first_seconds"] = first_seconds   # device time of the FP32 attempt before an FP64 re-solve
     return Solution(wn, yA.cpu().numpy().astype(np.float64)[:dp.P * dp.m].reshape(dp.P, dp.m) if yA is not None else None,
                     yD.cpu().numpy().astype(np.float64).reshape(dp.R, dp.n) if yD is not None else None,
                     info)

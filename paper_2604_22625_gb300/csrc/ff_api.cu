@@ -155,6 +155,8 @@ void fill_defaults(ff_options* o) {
     o->stall_checks = 48;
     o->round_panels_bf16 = 0;
     o->warm_start = 0;
+    o->panel_l2_keep = 1;
+    o->primal_weight = 0;
 }
 
 bool valid_options(const ff_options& o) {
@@ -177,6 +179,8 @@ bool valid_options(const ff_options& o) {
     if (o.stall_checks < 0) return false;
     if (o.round_panels_bf16 != 0 && o.round_panels_bf16 != 1) return false;
     if (o.warm_start != 0 && o.warm_start != 1) return false;
+    if (o.panel_l2_keep != 0 && o.panel_l2_keep != 1) return false;
+    if (o.primal_weight != 0 && o.primal_weight != 1) return false;
     return true;
 }
 
@@ -406,6 +410,8 @@ Params make_params(const ff_options& o) {
     prm.expire_first_wait = o.test_expire_first_wait;
     prm.stall_checks = o.stall_checks;
     prm.warm_start = o.warm_start;
+    prm.panel_keep = o.panel_l2_keep;
+    prm.primal_weight = o.primal_weight;
     prm.queue = nullptr;
     return prm;
 }

@@ -105,6 +105,8 @@ struct Params {
     int expire_first_wait;   // test hook (ff_options.test_expire_first_wait)
     int stall_checks;        // FP32/BF16 modes: checks without halving before FF_PRECISION (0 = off)
     int warm_start;          // 1: start from the output buffers (ff_options.warm_start)
+    int panel_keep;          // 1: panel-tile copies carry an L2 evict_last policy
+    int primal_weight;       // 1: adaptive primal weight at restarts (ff_options.primal_weight)
     int* queue;          // device counter of the next instance (zero at launch); teams take
                          // instances from it in table order
 };

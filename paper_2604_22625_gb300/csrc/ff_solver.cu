@@ -178,7 +178,25 @@ struct Pipe {
                               // until pipe_drain has let the copies in flight land
     int waits;                // waits of the current instance (the test hook expires the first)
     int expire_first;         // test hook: treat the instance's first wait as expired
+    int keep;                 // 1: panel tiles carry an L2 evict_last policy
+    unsigned long long policy;   // the L2 cache policy of the panel tiles (keep = 1)
 };
+
+// A panel-tile copy: with keep, the L2 policy asks to keep the panel's lines
+// (an instance re-reads its panel twice per iteration); per-asset vectors are
+// copied with the default policy.
+__device__ __forceinline__ void bulk_copy(unsigned dst, const void* src, unsigned bytes, unsigned bar, int keep,
+                                          unsigned long long policy) {
+    if (keep)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+            ::"r"(dst), "l"(src), "r"(bytes), "r"(bar), "l"(policy)
+            : "memory");
+    else
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
+                     : "memory");
+}
 
 constexpr int kWaitSpins = 1 << 22;    // try_wait polls of one wait before it counts as expired
 
@@ -204,9 +222,7 @@ __device__ __forceinline__ void pipe_issue(Pipe& pp, const void* src, unsigned b
         const unsigned bar = smem_u32(&pp.bars[pp.tail]);
         const unsigned dst = smem_u32(pp.ring + (size_t)pp.tail * pp.stride);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(dst), "l"(src), "r"(bytes), "r"(bar)
-                     : "memory");
+        bulk_copy(dst, src, bytes, bar, pp.keep, pp.policy);
     }
     pp.tail = pp.tail + 1 == kStages ? 0 : pp.tail + 1;
     ++pp.inflight;
@@ -223,11 +239,8 @@ __device__ __forceinline__ void pipe_issue_n(Pipe& pp, int nc, const void* const
         const unsigned bar = smem_u32(&pp.bars[pp.tail]);
         unsigned char* stage = pp.ring + (size_t)pp.tail * pp.stride;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(total) : "memory");
-        for (int q = 0; q < nc; ++q) {
-            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         ::"r"(smem_u32(stage + off[q])), "l"(src[q]), "r"(bytes[q]), "r"(bar)
-                         : "memory");
-        }
+        for (int q = 0; q < nc; ++q)   // copy 0 is the panel tile
+            bulk_copy(smem_u32(stage + off[q]), src[q], bytes[q], bar, q == 0 ? pp.keep : 0, pp.policy);
     }
     pp.tail = pp.tail + 1 == kStages ? 0 : pp.tail + 1;
     ++pp.inflight;
@@ -1305,6 +1318,9 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
     pipe.frozen = 0;
     pipe.waits = 0;
     pipe.expire_first = prm.expire_first_wait;
+    pipe.keep = prm.panel_keep;
+    pipe.policy = 0;
+    if (prm.panel_keep) asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pipe.policy));
     if (threadIdx.x == 0) { pipe_err_s = 0; ring_broken_s = 0; }
     pipe_init(pipe);
 
@@ -1432,16 +1448,36 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
         const double Lf = 2.0 * kap * lamS * 1.05;
         const double nA2 = (m > 0) ? fmax(lamA * 1.05, 1e-300) : 1.0;
         const double nD2 = c.I.multi ? 4.0 : 1.0;
-        const double tau = prm.step_fraction * 2.0 / Lf;
+        double tau = prm.step_fraction * 2.0 / Lf;
         // sigma_A ||A||^2 + sigma_D ||Delta||^2 = 1/tau - beta L_f (split evenly): the
         // gradient step is then beta-cocoercive in the step metric, the iteration map
         // is 2 beta / (4 beta - 1)-averaged, and reflection up to (2 beta - 1)/(2 beta)
         // keeps it nonexpansive (Condat 2013, Thm 3.1; averaged-operator calculus)
-        const double sig = (1.0 / tau - prm.beta * Lf) / ((m > 0) ? 2.0 : 1.0);
-        const double sA = sig / nA2;
-        const double sD = sig / nD2;
-        const double inv_sD = 1.0 / sD;
-        const double inv_sA = 1.0 / sA;
+        const double qsplit = (m > 0) ? 2.0 : 1.0;
+        const double sig = (1.0 / tau - prm.beta * Lf) / qsplit;
+        double sA = sig / nA2;
+        double sD = sig / nD2;
+        double inv_sD = 1.0 / sD;
+        double inv_sA = 1.0 / sA;
+        // Primal weight (adaptive steps, option primal_weight): omega = sqrt(sigma_D / tau),
+        // the ratio of the trade-block dual step to the primal step.  At a restart
+        // it moves halfway (in logarithm) toward ||dy|| / ||dx||, the distances
+        // the dual and the primal iterates travelled in the last cycle (PDLP's
+        // rule), and the steps are re-solved from the same budget,
+        //   1/tau = beta L_f + s,  sigma_A ||A||^2 + sigma_D ||Delta||^2 = s,
+        // with s (beta L_f + s) = omega^2 qsplit ||Delta||^2, so the Condat-Vu
+        // step condition keeps holding for every omega.
+        const double omega0 = sqrt(sD / tau);
+        double omega = omega0;
+        auto set_steps = [&](double om) {
+            const double bL = prm.beta * Lf;
+            const double sv = 0.5 * (-bL + sqrt(bL * bL + 4.0 * om * om * qsplit * nD2));
+            tau = 1.0 / (bL + sv);
+            sA = sv / (qsplit * nA2);
+            sD = sv / (qsplit * nD2);
+            inv_sD = 1.0 / sD;
+            inv_sA = 1.0 / sA;
+        };
         const double rho = prm.rho;
 
         // ---- initial point: w0 (single) / straight line w0 -> w_T (multi), or
@@ -1935,18 +1971,50 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                                     (prm.beta_art > 0 && (double)j >= prm.beta_art * (double)(it + 1));
             r_prev = fpr;
             if (do_restart) {
+                // distances travelled since the last restart (primal weight), then
+                // the current iterate becomes the anchor
+                double dl[3] = {0.0, 0.0, 0.0};
                 for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
-                    for (int p = 0; p < P; ++p) c.I.x0[(size_t)p * np + i] = c.I.x[(size_t)p * np + i];
-                    for (int r = 0; r < R; ++r) c.I.yD0[(size_t)r * np + i] = c.I.yD[(size_t)r * np + i];
+                    for (int p = 0; p < P; ++p) {
+                        const size_t o = (size_t)p * np + i;
+                        double dd;
+                        if constexpr (kIncr) dd = (double)df_sub(((const float2*)c.I.x)[o], ((const float2*)c.I.x0)[o]);
+                        else dd = c.I.x[o] - c.I.x0[o];
+                        dl[0] += dd * dd;
+                        c.I.x0[o] = c.I.x[o];
+                    }
+                    for (int r = 0; r < R; ++r) {
+                        const size_t o = (size_t)r * np + i;
+                        double dd;
+                        if constexpr (kIncr) dd = (double)df_sub(((const float2*)c.I.yD)[o], ((const float2*)c.I.yD0)[o]);
+                        else dd = c.I.yD[o] - c.I.yD0[o];
+                        dl[1] += dd * dd;
+                        c.I.yD0[o] = c.I.yD[o];
+                    }
                 }
+                for (int e = c.tid; e < P * m; e += kThreads) {
+                    const double dd = c.yA[e] - c.I.yA0[e];   // replicated: counted once below
+                    dl[2] += dd * dd;
+                }
+                __syncthreads();
                 for (int e = c.tid; e < P * m; e += kThreads) c.I.yA0[e] = c.yA[e];
                 // the new anchor is read by bulk copies (async proxy) from here on
                 asm volatile("fence.proxy.async.global;" ::: "memory");
+                block_reduce<3>(dl, c.spart, c.wred, c.lane, c.warp);
+                const double dyA = c.spart[2];
+                team_reduce<false>(cl, c.spart, c.sout, 2, G, g);
+                const double dx = sqrt(c.sout[0]), dy = sqrt(c.sout[1] + dyA);
                 __syncthreads();
                 j = 0;
                 ++restarts;
                 r_restart = fpr;
                 r_prev = INFINITY;
+                if (prm.primal_weight && dx > 1e-30 && dy > 1e-30) {
+                    const double target = fmin(fmax(dy / dx, 1e-4 * omega0), 1e4 * omega0);
+                    omega = exp(0.5 * log(target) + 0.5 * log(omega));
+                    set_steps(omega);
+                    r_restart = -1.0;   // the next check measures in the new step metric
+                }
             }
         }
 
