@@ -95,12 +95,14 @@ def escalation_options(opts: L.ff_options) -> L.ff_options:
     """Options of the FP64 re-solve of an instance that ended with
     FF_PRECISION in the FP32 or BF16 mode: the same tolerances and limits in
     FF_PREC_F64, with F and A rounded to bfloat16 in the repack when the first
-    solve was BF16 (so both solves see the same data)."""
+    solve was BF16 (so both solves see the same data), warm-started from the
+    point the FP32 solve returned (its output buffers)."""
     o = L.ff_options()
     C.pointer(o)[0] = opts
     o.round_panels_bf16 = 1 if opts.precision == L.FF_PREC_BF16 else 0
     o.precision = L.FF_PREC_F64
     o.reuse_workspace = 0
+    o.warm_start = 1
     return o
 
 
@@ -139,7 +141,6 @@ def solve(prob, precision: str = "f32", device: str = "cuda", return_duals: bool
             yD.zero_()
             if warm.yD is not None:
                 yD.copy_(torch.as_tensor(np.asarray(warm.yD).reshape(-1), dtype=dtype))
-    w0_state = (w.clone(), None if yA is None else yA.clone(), None if yD is None else yD.clone())
 
     def call(o, nbytes):
         ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
@@ -155,11 +156,7 @@ def solve(prob, precision: str = "f32", device: str = "cuda", return_duals: bool
     first_seconds = 0.0
     if escalate and int(rec["status"]) == L.FF_PRECISION and opts.precision != L.FF_PREC_F64:
         first_seconds = float(rec["seconds"])
-        o64 = escalation_options(opts)
-        if warm is not None:       # the FP64 re-solve starts from the same point
-            for dst, src in zip((w, yA, yD), w0_state):
-                if dst is not None:
-                    dst.copy_(src)
+        o64 = escalation_options(opts)     # starts from the FP32 attempt's point in w, yA, yD
         rec = call(o64, L.ff_workspace_size(C.byref(dp.struct), 1, o64))
         escalated = True
     wn = w.cpu().numpy().astype(np.float64)

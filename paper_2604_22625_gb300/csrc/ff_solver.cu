@@ -453,10 +453,11 @@ __device__ void team_reduce_mixed(cg::cluster_group& cl, double* part, double* o
         double v[kMaxCluster];
 #pragma unroll
         for (int q = 0; q < kMaxCluster; ++q)
-            v[q] = (q < G) ? cl.map_shared_rank(part, q)[idx] : (mx ? -INFINITY : 0.0);
+            if (q < G) v[q] = cl.map_shared_rank(part, q)[idx];
         double s = v[0];
 #pragma unroll
-        for (int q = 1; q < kMaxCluster; ++q) s = mx ? fmax(s, v[q]) : s + v[q];
+        for (int q = 1; q < kMaxCluster; ++q)
+            if (q < G) s = mx ? fmax(s, v[q]) : s + v[q];
         for (int q = 0; q < G; ++q) cl.map_shared_rank(out, q)[idx] = s;
     }
     cl.sync();
@@ -472,10 +473,11 @@ __device__ void team_reduce(cg::cluster_group& cl, double* part, double* out, in
         double v[kMaxCluster];
 #pragma unroll
         for (int q = 0; q < kMaxCluster; ++q)
-            v[q] = (q < G) ? cl.map_shared_rank(part, q)[idx] : (MAX ? -INFINITY : 0.0);
+            if (q < G) v[q] = cl.map_shared_rank(part, q)[idx];
         double s = v[0];
 #pragma unroll
-        for (int q = 1; q < kMaxCluster; ++q) s = MAX ? fmax(s, v[q]) : s + v[q];
+        for (int q = 1; q < kMaxCluster; ++q)
+            if (q < G) s = MAX ? fmax(s, v[q]) : s + v[q];
         for (int q = 0; q < G; ++q) cl.map_shared_rank(out, q)[idx] = s;
     }
     cl.sync();
@@ -796,6 +798,8 @@ __device__ void reduce_fused_single(Ctx<M, S>& c, double hlA, double hlB, double
                              po + 40u * CH + (unsigned)sizeof(M) * CH};
     M* st = c.stage;  // [2][CH]: x_bar, x+
     const double theta = c.theta[0];
+    // FP32 copies of the pass's scalars, converted once (not per element)
+    const float fA = (float)hlA, fC = (float)hlC, fsD = (float)sD, finv = (float)inv_sD, th = (float)theta;
     for (int e = c.tid; e < Lr; e += kThreads) c.vpart[e] = 0;
     const ReduceMap mp = reduce_map(c);
     ReduceAcc<1, M> acc;
@@ -829,10 +833,8 @@ __device__ void reduce_fused_single(Ctx<M, S>& c, double hlA, double hlB, double
             const int i = ib + ii;
             if constexpr (std::is_same<M, float>::value) {
                 // FP32 increments on the double-float state (see the multi-period pass)
-                const float fA = (float)hlA, fC = (float)hlC, fsD = (float)sD, finv = (float)inv_sD;
                 const float2 vu = ((const float2*)c.I.v)[i];
                 const float2 xc = ((const float2*)sx)[ii];
-                const float th = (float)theta;
                 const float av = fabsf(vu.x) - th;
                 float d1, xbf = 0.f;
                 if (av > 0.f) {
@@ -1052,6 +1054,7 @@ __device__ void expand_main_single(Ctx<M, S>& c, double tau, double kap, const M
     const unsigned po = c.panel_off;
     const unsigned off[5] = {0u, po, po + 8u * CH, po + 16u * CH, po + 16u * CH + (unsigned)sizeof(M) * CH};
     const M kapm = (M)kap;
+    const float ftau = (float)tau;
     double* v = c.I.v;
     auto issue = [&](int t) {
         const int ib = t * CH;
@@ -1082,7 +1085,7 @@ __device__ void expand_main_single(Ctx<M, S>& c, double tau, double kap, const M
                 const float xf = ((const float2*)sx)[ii].x;
                 const float gf = -sal[ii] + 2.f * kapm * ((float)aF + sdp[ii] * xf);
                 const float kt = (float)aA + ((const float2*)syd)[ii].x;
-                const float u = -(float)tau * (gf + kt);
+                const float u = -ftau * (gf + kt);
                 ((float2*)v)[i] = make_float2(xf + u, u);
             } else {
                 const M gf = -sal[ii] + (M)2 * kapm * ((M)aF + sdp[ii] * (M)xv);
@@ -1306,6 +1309,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
     __shared__ int next_s;
     __shared__ int pipe_err_s;
     __shared__ int ring_broken_s;   // a copy never landed: no further copies on this CTA
+    __shared__ int decide_s[2];     // rank 0's decisions at a check: stop status (-1: go on), restart
     Pipe pipe;
     pipe.bars = (unsigned long long*)smem;   // the layout puts the barriers first
     pipe.ring = nullptr;
@@ -1640,6 +1644,10 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                 const M* __restrict__ c1a = c.I.c1;
                 const M* __restrict__ c2a = c.I.c2;
                 const float fA = (float)hlA, fC = (float)hlC, fsD = (float)sD, finv = (float)inv_sD;
+                // the thresholds in FP32, once per period (not per element)
+                __shared__ float thf_s[64];
+                for (int r = c.tid; r < P; r += kThreads) thf_s[r] = (float)c.theta[r];
+                __syncthreads();
                 for (int i = c.i0 + c.tid; i < c.i1; i += kThreads) {
                     const float2 w0v = c.I.w0f[i];
                     const float2 wtv = c.I.multi ? c.I.cen2[i] : make_float2(0.f, 0.f);
@@ -1659,7 +1667,7 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                         }
                         float d1 = 0.f;
                         if (r < P) {
-                            const float th = (float)c.theta[r];
+                            const float th = thf_s[r];
                             const float av = fabsf(vu.x) - th;
                             float xbf = 0.f;
                             if (av > 0.f) {
@@ -1944,32 +1952,56 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
             res_rel = rel; res_p = r_p; res_d = r_d; res_g = r_g; res_P = Pobj; res_D = Dobj; res_T = phi_terms;
             r_last = fpr;
             lap(5);
-            if (sums[12] > 0) { status = FF_STALLED; break; }
-            // every part is tested: fmax would pass over a NaN in one of them
-            if (!(r_p == r_p) || !(r_d == r_d) || !(r_g == r_g) || !(fpr == fpr) || !(Pobj == Pobj) ||
-                !(Dobj == Dobj) || isinf(Pobj) || isinf(Dobj)) {
-                res_rel = NAN;
-                status = FF_NUMERICAL;
+            int st_new = -1;   // a stop status, or -1 to go on
+            if (sums[12] > 0) {
+                st_new = FF_STALLED;
+            } else if (!(r_p == r_p) || !(r_d == r_d) || !(r_g == r_g) || !(fpr == fpr) || !(Pobj == Pobj) ||
+                       !(Dobj == Dobj) || isinf(Pobj) || isinf(Dobj)) {
+                // every part is tested: fmax would pass over a NaN in one of them
+                st_new = FF_NUMERICAL;
+            } else if (rel <= prm.tol) {
+                st_new = FF_CONVERGED;
+            } else if (sums[11] > prm.time_limit_ns) {
+                st_new = FF_TIME_LIMIT;
+            } else {
+                // precision floor of the FP32/BF16 modes: no halving of the relative
+                // KKT residual over stall_checks checks (the rounding of the FP32
+                // products then bounds it; the host re-solves such instances in FP64)
+                if (rel <= 0.5 * stall_ref) { stall_ref = rel; stall_n = 0; }
+                else ++stall_n;
+                if (kIncr && prm.stall_checks > 0 && stall_n >= prm.stall_checks) st_new = FF_PRECISION;
+            }
+            bool do_restart = false;
+            if (st_new < 0) {
+                // restart on the fixed-point residual: sufficient decay, necessary
+                // decay that stalls, or (artificial) once the current restart cycle
+                // holds a fixed share of all iterations so far; the anchor becomes
+                // the current iterate
+                if (r_restart < 0) r_restart = fpr;
+                do_restart = (fpr <= prm.beta_suff * r_restart) ||
+                             (fpr <= prm.beta_nec * r_restart && fpr > r_prev) ||
+                             (prm.beta_art > 0 && (double)j >= prm.beta_art * (double)(it + 1));
+                r_prev = fpr;
+            }
+            // every CTA of the team takes rank 0's decisions (they are computed from
+            // bit-identical team sums; the broadcast keeps the team's control flow,
+            // and so its cluster barriers, uniform by construction)
+            if (g == 0 && c.tid == 0) {
+                decide_s[0] = st_new;
+                decide_s[1] = do_restart ? 1 : 0;
+            }
+            cl.sync();
+            {
+                const int* d0 = cl.map_shared_rank(decide_s, 0);
+                st_new = d0[0];
+                do_restart = d0[1] != 0;
+            }
+            cl.sync();
+            if (st_new >= 0) {
+                if (st_new == FF_NUMERICAL) res_rel = NAN;
+                status = st_new;
                 break;
             }
-            if (rel <= prm.tol) { status = FF_CONVERGED; break; }
-            if (sums[11] > prm.time_limit_ns) { status = FF_TIME_LIMIT; break; }
-            // precision floor of the FP32/BF16 modes: no halving of the relative
-            // KKT residual over stall_checks checks (the rounding of the FP32
-            // products then bounds it; the host re-solves such instances in FP64)
-            if (rel <= 0.5 * stall_ref) { stall_ref = rel; stall_n = 0; }
-            else ++stall_n;
-            if (kIncr && prm.stall_checks > 0 && stall_n >= prm.stall_checks) { status = FF_PRECISION; break; }
-            // restart on the fixed-point residual (sufficient / necessary decay);
-            // the anchor becomes the current iterate
-            if (r_restart < 0) r_restart = fpr;
-            // restart on sufficient decay, on necessary decay that stalls, or
-            // (artificial) once the current restart cycle holds a fixed share
-            // of all iterations so far
-            const bool do_restart = (fpr <= prm.beta_suff * r_restart) ||
-                                    (fpr <= prm.beta_nec * r_restart && fpr > r_prev) ||
-                                    (prm.beta_art > 0 && (double)j >= prm.beta_art * (double)(it + 1));
-            r_prev = fpr;
             if (do_restart) {
                 // distances travelled since the last restart (primal weight), then
                 // the current iterate becomes the anchor
@@ -1992,18 +2024,23 @@ team_kernel(const Inst<M, S>* __restrict__ insts, int count, Params prm) {
                         c.I.yD0[o] = c.I.yD[o];
                     }
                 }
-                for (int e = c.tid; e < P * m; e += kThreads) {
-                    const double dd = c.yA[e] - c.I.yA0[e];   // replicated: counted once below
-                    dl[2] += dd * dd;
-                }
-                __syncthreads();
+                // y_A and its anchor are replicated in every CTA of the team (the
+                // anchor in one global array that every CTA writes with the same
+                // values): rank 0 alone counts their distance, and no CTA writes the
+                // new anchor before the team reduction below, whose cluster barriers
+                // order every CTA's reads of the old anchor before those writes; so
+                // every CTA holds bit-identical distances and takes the same decisions
+                if (g == 0)
+                    for (int e = c.tid; e < P * m; e += kThreads) {
+                        const double dd = c.yA[e] - c.I.yA0[e];
+                        dl[2] += dd * dd;
+                    }
+                block_reduce<3>(dl, c.spart, c.wred, c.lane, c.warp);
+                team_reduce<false>(cl, c.spart, c.sout, 3, G, g);
+                const double dx = sqrt(c.sout[0]), dy = sqrt(c.sout[1] + c.sout[2]);
                 for (int e = c.tid; e < P * m; e += kThreads) c.I.yA0[e] = c.yA[e];
                 // the new anchor is read by bulk copies (async proxy) from here on
                 asm volatile("fence.proxy.async.global;" ::: "memory");
-                block_reduce<3>(dl, c.spart, c.wred, c.lane, c.warp);
-                const double dyA = c.spart[2];
-                team_reduce<false>(cl, c.spart, c.sout, 2, G, g);
-                const double dx = sqrt(c.sout[0]), dy = sqrt(c.sout[1] + dyA);
                 __syncthreads();
                 j = 0;
                 ++restarts;
