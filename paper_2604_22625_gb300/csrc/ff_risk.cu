@@ -41,47 +41,105 @@ __host__ __device__ inline int tri(int p) { return p * (p + 1) / 2; }
 __host__ __device__ inline size_t window_doubles(int T, int p) { return (size_t)(T + 1) * (tri(p) + p); }
 
 __global__ void risk_prep_kernel(const float* __restrict__ F, int T, int p, double* __restrict__ sigma_f,
-                                 double* __restrict__ tables) {
+                                 double* __restrict__ tables, double* __restrict__ ginv0) {
     extern __shared__ float fsh[];   // [T][p] factor returns of this window
+    constexpr int kSeg = 8;          // row segments of the parallel suffix scan
+    __shared__ double seg_tot[kSeg][kMaxP * (kMaxP + 1) / 2 + kMaxP];
+    __shared__ double mean_s[kMaxP];
+    __shared__ double cov_part[kMaxP * kMaxP][4];
     const int d = blockIdx.x;
     const float* fg = F + (size_t)d * T * p;
     for (int e = threadIdx.x; e < T * p; e += blockDim.x) fsh[e] = fg[e];
     __syncthreads();
     const float* f = fsh;
     double* tab = tables + (size_t)d * window_doubles(T, p);
-    const int np = tri(p);
-    __shared__ double mean_s[kMaxP];
-    // suffix sums: entry e < np is the Gram entry (a, b), a <= b; e >= np the sum of f_a
-    for (int e = threadIdx.x; e < np + p; e += blockDim.x) {
+    const int np = tri(p), ne = np + p;
+    // suffix sums, entry e < np the Gram entry (a, b) with a <= b, e >= np the sum of
+    // f_a: segment totals, then the segment offsets, then each segment's running sums
+    auto entry = [&](int e, int k) -> double {
         int a = 0, b = 0;
         if (e < np) {
             int r = e;
             while (r >= p - a) { r -= p - a; ++a; }
             b = a + r;
-        } else {
-            a = e - np;
+            return (double)f[(size_t)k * p + a] * (double)f[(size_t)k * p + b];
         }
+        return (double)f[(size_t)k * p + (e - np)];
+    };
+    for (int w = threadIdx.x; w < ne * kSeg; w += blockDim.x) {
+        const int e = w % ne, sg = w / ne;
+        const int k0 = (int)((long long)T * sg / kSeg), k1 = (int)((long long)T * (sg + 1) / kSeg);
         double acc = 0.0;
-        tab[(size_t)T * (np + p) + e] = 0.0;
-        for (int k = T - 1; k >= 0; --k) {
-            const double fa = (double)f[(size_t)k * p + a];
-            acc += e < np ? fa * (double)f[(size_t)k * p + b] : fa;
-            tab[(size_t)k * (np + p) + e] = acc;
-        }
-    }
-    // factor covariance: mean-removed, divisor T - 1
-    for (int a = threadIdx.x; a < p; a += blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < T; ++k) s += (double)f[(size_t)k * p + a];
-        mean_s[a] = s / (double)T;
+        for (int k = k0; k < k1; ++k) acc += entry(e, k);
+        seg_tot[sg][e] = acc;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    for (int w = threadIdx.x; w < ne * kSeg; w += blockDim.x) {
+        const int e = w % ne, sg = w / ne;
+        const int k0 = (int)((long long)T * sg / kSeg), k1 = (int)((long long)T * (sg + 1) / kSeg);
+        double acc = 0.0;
+        for (int q = kSeg - 1; q > sg; --q) acc += seg_tot[q][e];   // rows after this segment
+        if (sg == kSeg - 1) tab[(size_t)T * ne + e] = 0.0;
+        for (int k = k1 - 1; k >= k0; --k) {
+            acc += entry(e, k);
+            tab[(size_t)k * ne + e] = acc;
+        }
+    }
+    // factor covariance: mean-removed, divisor T - 1 (4 partial sums per entry)
+    for (int a = threadIdx.x; a < p; a += blockDim.x) {
+        double sm = 0.0;
+        for (int k = 0; k < T; ++k) sm += (double)f[(size_t)k * p + a];
+        mean_s[a] = sm / (double)T;
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < p * p * 4; w += blockDim.x) {
+        const int e = w % (p * p), part = w / (p * p);
         const int a = e / p, b = e % p;
-        double s = 0.0;
-        for (int k = 0; k < T; ++k)
-            s += ((double)f[(size_t)k * p + a] - mean_s[a]) * ((double)f[(size_t)k * p + b] - mean_s[b]);
-        sigma_f[(size_t)d * p * p + e] = s / (double)(T - 1);
+        double sm = 0.0;
+        for (int k = part; k < T; k += 4)
+            sm += ((double)f[(size_t)k * p + a] - mean_s[a]) * ((double)f[(size_t)k * p + b] - mean_s[b]);
+        cov_part[e][part] = sm;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x)
+        sigma_f[(size_t)d * p * p + e] =
+            (((cov_part[e][0] + cov_part[e][1]) + cov_part[e][2]) + cov_part[e][3]) / (double)(T - 1);
+    // inverse of the whole window's Gram matrix (stocks with a return on every day):
+    // Cholesky and p back-substitutions by one thread (p <= 8)
+    if (threadIdx.x == 0) {
+        double Lm[kMaxP][kMaxP];
+        int e = 0;
+        for (int a = 0; a < p; ++a)
+            for (int b = a; b < p; ++b, ++e) { Lm[b][a] = tab[e]; Lm[a][b] = tab[e]; }
+        bool spd = true;
+        for (int a = 0; a < p; ++a) {
+            double sv = Lm[a][a];
+            for (int c = 0; c < a; ++c) sv -= Lm[a][c] * Lm[a][c];
+            if (!(sv > 0.0)) { spd = false; sv = 1.0; }
+            const double l = sqrt(sv);
+            Lm[a][a] = l;
+            for (int r = a + 1; r < p; ++r) {
+                double t = Lm[r][a];
+                for (int c = 0; c < a; ++c) t -= Lm[r][c] * Lm[a][c];
+                Lm[r][a] = t / l;
+            }
+        }
+        double* gi = ginv0 + (size_t)d * (kMaxP * kMaxP + 1);
+        for (int col = 0; col < p; ++col) {
+            double y[kMaxP], x[kMaxP];
+            for (int a = 0; a < p; ++a) {
+                double t = (a == col) ? 1.0 : 0.0;
+                for (int c = 0; c < a; ++c) t -= Lm[a][c] * y[c];
+                y[a] = t / Lm[a][a];
+            }
+            for (int a = p - 1; a >= 0; --a) {
+                double t = y[a];
+                for (int c = a + 1; c < p; ++c) t -= Lm[c][a] * x[c];
+                x[a] = t / Lm[a][a];
+            }
+            for (int a = 0; a < p; ++a) gi[a * p + col] = x[a];
+        }
+        gi[kMaxP * kMaxP] = spd ? 1.0 : 0.0;
     }
 }
 
@@ -178,12 +236,30 @@ risk_stream_kernel(const float* __restrict__ F, const float* __restrict__ R, int
     }
 }
 
+// beta and the residual variance from the moments: sum theta = s1 - beta^T g1,
+// sum theta^2 = s2 - beta^T b (at the least-squares solution)
+template <int P>
+__device__ __forceinline__ void finish_moments(const double (&x)[P], const double (&b)[P], const double (&g1)[P],
+                                               const double* s, int cnt, double* bo, double* Dout) {
+    double bt_b = 0.0, bt_g = 0.0;
+#pragma unroll
+    for (int j = 0; j < P; ++j) {
+        bo[j] = x[j];
+        bt_b += x[j] * b[j];
+        bt_g += x[j] * g1[j];
+    }
+    const double st = s[P] - bt_g;
+    const double sq = s[P + 1] - bt_b;
+    *Dout = (sq - st * st / (double)cnt) / (double)(cnt - 1);
+}
+
 // One thread per stock: history rule, normal equations over the stock's days
 // (suffix Gram table, FP64 Cholesky), residual variance from the moments.
 template <int P>
 __global__ void risk_finish_kernel(int T, int n, int min_obs, const double* __restrict__ tables,
-                                   const double* __restrict__ sums, const int* __restrict__ hist,
-                                   double* __restrict__ beta, double* __restrict__ D, int32_t* __restrict__ nobs) {
+                                   const double* __restrict__ ginv0, const double* __restrict__ sums,
+                                   const int* __restrict__ hist, double* __restrict__ beta, double* __restrict__ D,
+                                   int32_t* __restrict__ nobs) {
     constexpr int NS = P + 2;
     const int d = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -203,17 +279,30 @@ __global__ void risk_finish_kernel(int T, int n, int min_obs, const double* __re
     }
     constexpr int NP = P * (P + 1) / 2;
     const double* tab = tables + (size_t)d * window_doubles(T, P) + (size_t)first * (NP + P);
-    double Lm[P][P];
-    {
-        int e = 0;
-        for (int a = 0; a < P; ++a)
-            for (int b = a; b < P; ++b, ++e) { Lm[b][a] = tab[e]; Lm[a][b] = tab[e]; }
-    }
-    double b[P], g1[P];
+    double b[P], g1[P], x[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
         b[j] = sums[si * NS + j];
         g1[j] = tab[NP + j];
+    }
+    const double* gi = ginv0 + (size_t)d * (kMaxP * kMaxP + 1);
+    if (first == 0 && gi[kMaxP * kMaxP] != 0.0) {
+        // a return on every day: the window's Gram inverse, computed once per window
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            double t = 0.0;
+#pragma unroll
+            for (int c2 = 0; c2 < P; ++c2) t += gi[a * P + c2] * b[c2];
+            x[a] = t;
+        }
+        finish_moments<P>(x, b, g1, sums + si * NS, cnt, beta + si * P, D + si);
+        return;
+    }
+    double Lm[P][P];
+    {
+        int e = 0;
+        for (int a = 0; a < P; ++a)
+            for (int bb = a; bb < P; ++bb, ++e) { Lm[bb][a] = tab[e]; Lm[a][bb] = tab[e]; }
     }
     bool spd = true;
 #pragma unroll
@@ -229,7 +318,7 @@ __global__ void risk_finish_kernel(int T, int n, int min_obs, const double* __re
             Lm[r][a] = t / l;
         }
     }
-    double y[P], x[P];
+    double y[P];
 #pragma unroll
     for (int a = 0; a < P; ++a) {
         double t = b[a];
@@ -249,23 +338,13 @@ __global__ void risk_finish_kernel(int T, int n, int min_obs, const double* __re
         if (nobs) nobs[si] = -2;
         return;
     }
-    // residual moments: sum theta = s1 - beta^T g1, sum theta^2 = s2 - beta^T b (at the solution)
-    double bt_b = 0.0, bt_g = 0.0;
-#pragma unroll
-    for (int j = 0; j < P; ++j) {
-        bo[j] = x[j];
-        bt_b += x[j] * b[j];
-        bt_g += x[j] * g1[j];
-    }
-    const double st = sums[si * NS + P] - bt_g;
-    const double sq = sums[si * NS + P + 1] - bt_b;
-    D[si] = (sq - st * st / (double)cnt) / (double)(cnt - 1);
+    finish_moments<P>(x, b, g1, sums + si * NS, cnt, bo, D + si);
 }
 
 template <int P>
 cudaError_t launch_stream(const float* F, const float* R, int count, int T, int n, int min_obs,
-                          const double* tables, double* sums, int* hist, double* beta, double* D, int32_t* nobs,
-                          cudaStream_t stream) {
+                          const double* tables, const double* ginv0, double* sums, int* hist, double* beta,
+                          double* D, int32_t* nobs, cudaStream_t stream) {
     const size_t smem = (size_t)T * P * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(risk_stream_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -275,7 +354,7 @@ cudaError_t launch_stream(const float* F, const float* R, int count, int T, int 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 grid2((unsigned)((n + 127) / 128), (unsigned)count);
-    risk_finish_kernel<P><<<grid2, 128, 0, stream>>>(T, n, min_obs, tables, sums, hist, beta, D, nobs);
+    risk_finish_kernel<P><<<grid2, 128, 0, stream>>>(T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs);
     return cudaGetLastError();
 }
 
@@ -293,7 +372,8 @@ int risk_fail(cudaError_t e, const char* where) {
 extern "C" {
 
 static size_t risk_tables_bytes(int count, int T, int p) {
-    return ((size_t)count * ff::window_doubles(T, p) * sizeof(double) + 255) / 256 * 256;
+    // suffix tables, then the inverse Gram matrix of every window (kMaxP^2 + 1 doubles)
+    return ((size_t)count * (ff::window_doubles(T, p) + ff::kMaxP * ff::kMaxP + 1) * sizeof(double) + 255) / 256 * 256;
 }
 
 size_t ff_risk_workspace_size(int count, int T, int n, int p) {
@@ -311,23 +391,24 @@ int ff_risk_estimate(int count, int T, int n, int p, const float* F, const float
     if ((long long)(n + ff::kRiskThreads - 1) / ff::kRiskThreads > 2147483647LL) return FF_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
     double* tables = (double*)ws;
+    double* ginv0 = tables + (size_t)count * ff::window_doubles(T, p);
     double* sums = (double*)((unsigned char*)ws + risk_tables_bytes(count, T, p));
     int* hist = (int*)((unsigned char*)sums + ((size_t)count * n * (p + 2) * sizeof(double) + 255) / 256 * 256);
     const size_t fsmem = (size_t)T * p * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(ff::risk_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
     if (e != cudaSuccess) return ff::risk_fail(e, "risk_prep_kernel attribute");
-    ff::risk_prep_kernel<<<count, 64, fsmem, st>>>(F, T, p, sigma_f, tables);
+    ff::risk_prep_kernel<<<count, 256, fsmem, st>>>(F, T, p, sigma_f, tables, ginv0);
     e = cudaGetLastError();
     if (e != cudaSuccess) return ff::risk_fail(e, "risk_prep_kernel launch");
     switch (p) {
-        case 1: e = ff::launch_stream<1>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
-        case 2: e = ff::launch_stream<2>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
-        case 3: e = ff::launch_stream<3>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
-        case 4: e = ff::launch_stream<4>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
-        case 5: e = ff::launch_stream<5>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
-        case 6: e = ff::launch_stream<6>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
-        case 7: e = ff::launch_stream<7>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
-        default: e = ff::launch_stream<8>(F, R, count, T, n, min_obs, tables, sums, hist, beta, D, nobs, st); break;
+        case 1: e = ff::launch_stream<1>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
+        case 2: e = ff::launch_stream<2>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
+        case 3: e = ff::launch_stream<3>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
+        case 4: e = ff::launch_stream<4>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
+        case 5: e = ff::launch_stream<5>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
+        case 6: e = ff::launch_stream<6>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
+        case 7: e = ff::launch_stream<7>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
+        default: e = ff::launch_stream<8>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
     }
     if (e != cudaSuccess) return ff::risk_fail(e, "risk_stream_kernel launch");
     return FF_OK;
