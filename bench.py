@@ -453,19 +453,26 @@ def run_ours(args):
         runner.capture(stream)
     escalated_steps = []
 
+    bw_ev = []   # (start, end) events of the backward pass of each step (diff workload)
+
     def step(s_):
         if use_graph:
             runner.replay(s_)
         else:
             runner.run(s_)
-        if diff:
-            runner.backward(s_)
         escalated_steps.append(runner.finish(s_))
+        if diff:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s_)
+            runner.backward(s_)
+            e1.record(s_)
+            bw_ev.append((e0, e1))
 
     for _ in range(args.warmup):
         step(stream)
     torch.cuda.synchronize(dev)
     escalated_steps.clear()
+    bw_ev.clear()
 
     # the oracle check starts on the warm-up outputs (the timed steps solve the
     # same inputs; their outputs are compared bit for bit below) and runs in
@@ -643,6 +650,8 @@ def run_ours(args):
             "solved": solved, "max_rel_kkt": kkt_max,
             "escalated_fp64": max(escalated_steps, default=0),
             "iterations_mean": float(statistics.mean(iters)),
+            "backward_ms": [a.elapsed_time(b) for a, b in bw_ev] if diff else None,
+            "backward_status": ([int(v) for v in runner.bstatus.cpu().tolist()] if diff else None),
             "instance_seconds": {"sum": float(sum(inst_s)), "max": float(max(inst_s))},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
@@ -797,14 +806,15 @@ def run_risk(args):
                        "precision": "float32 returns; FP32 chunk sums folded into double-float; FP64 solves"},
             "roofline": {"bound": "hbm", "achieved": alg / mean_s / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": alg / mean_s / 1e9 / peak, "traffic": None,
-                         "kernel": "risk_prep_kernel + risk_stream_kernel (one call)",
+                         "kernel": "risk_prep_kernel + risk_stream_kernel + risk_finish_kernel (one "
+                                   "ff_risk_estimate call, timed as a whole)",
                          "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
             "oracle_check": check,
             "cpu_baseline": {"value": 1.0 / cpu_s, "unit": unit, "cores": cpu_cores(), "kind": "oracle",
                              "sample": "one window (all 5000 stocks) solved by the oracle"},
             "e2e": {"value": count / e2e_s, "unit": unit, "h2d_bytes_per_step": int(Fh.numel() * 4 + Rh.numel() * 4),
                     "d2h_bytes_per_step": int(out_b.numel() * 8 + out_d.numel() * 8)},
-            "gpu_launches": 2 * steps, "clocks": clocks, "step_ms": ms}
+            "gpu_launches": 3 * steps, "clocks": clocks, "step_ms": ms}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

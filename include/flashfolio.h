@@ -344,11 +344,16 @@ size_t ff_backward_multi_workspace_size(const ff_problem* probs, int count);
  *       m = 0), yD T x n, grad_w (T-1) x n, all of the problem's dtype.
  *   status_dev : device array of count int32 or NULL: 0 ok, 3 the conjugate
  *       gradients reached their iteration limit (600), 4 a non-positive or
- *       non-finite curvature / residual was met (degenerate active set).
+ *       non-finite curvature / residual was met (degenerate active set), 5 a
+ *       bounded wait at a grid barrier expired (outputs undefined).
  *   ws : device workspace of ff_backward_multi_workspace_size bytes, 256-byte
  *       aligned; its contents are overwritten.
- * Asynchronous on `stream` (about 6,000 kernel launches; no host
- * synchronisation); FF_OK or an FF_ERR_* code. */
+ * Asynchronous on `stream`: one cooperative kernel launch (the phases of the
+ * computation are separated by grid barriers; every wait at a barrier is
+ * bounded, and a wait that expires ends every instance with status 5) after
+ * a host-to-device copy of the instance table and a memset of the barrier
+ * state; no host synchronisation.  FF_ERR_UNSUPPORTED if the device has no
+ * cooperative launch; FF_OK or an FF_ERR_* code. */
 int ff_backward_multi_batch(const ff_problem* probs, int count, const void* const* w, const void* const* yA,
                             const void* const* yD, const void* const* grad_w, const ff_grads* out, void* ws,
                             size_t ws_bytes, int32_t* status_dev, void* stream);

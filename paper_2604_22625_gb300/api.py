@@ -427,21 +427,9 @@ class BatchRunner:
 
     def backward_launches(self) -> int:
         """Kernels one ``backward()`` enqueues: one for the single-period
-        instances; for the multi-period ones setup (2), the assembly of
-        E M^-1 E^T in passes of 32 columns (2 per pass), its factor and
-        inverse (2), the first projection (6), 600 conjugate-gradient
-        iterations of 10 launches (converged instances return at once) and
-        the gradient assembly (7) -- the launch sequence of
-        ff_backward_multi_batch."""
-        total = 0
-        for idx, *_ in self._bsets:
-            if int(self.problems[idx[0]].T) < 2:
-                total += 1
-            else:
-                rmax = max((int(self.problems[i].T) - 1) * (int(np.asarray(self.problems[i].A).shape[0]) + 1)
-                           for i in idx)
-                total += 2 + 2 * ((rmax + 31) // 32) + 2 + 6 + 600 * 10 + 7
-        return total
+        instances and one cooperative launch for the multi-period ones (the
+        launch sequence of ff_backward_batch and ff_backward_multi_batch)."""
+        return len(self._bsets)
 
     @property
     def bstatus(self) -> torch.Tensor:

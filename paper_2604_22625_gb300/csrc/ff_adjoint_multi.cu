@@ -32,9 +32,11 @@
 // projection onto null(E) uses C = E M^{-1} E^T, assembled once, factored by a
 // Cholesky that drops dependent rows, and inverted explicitly so that each
 // iteration applies it as a matrix-vector product.  The multipliers nu are the
-// accumulated projection coefficients.  Every step is a separate kernel over
-// all instances of the batch (grid.y = instance); no kernel waits on another
-// block.  FP64 throughout.
+// accumulated projection coefficients.  The whole computation is one
+// cooperative launch over all instances of the batch: each step is a phase
+// spread over the grid, phases are separated by a grid barrier whose waits are
+// bounded, and the conjugate-gradient loop ends when every instance has
+// stopped.  FP64 throughout.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -48,8 +50,7 @@
 namespace ff {
 namespace {
 
-constexpr int kMT = 128;              // threads of the per-asset / per-element kernels
-constexpr int kRT = 256;              // threads of the per-row kernels (8 warps)
+constexpr int kRT = 256;              // threads of a block (8 warps)
 constexpr int kNB = 32;               // columns of M^{-1} E^T per pass while C is assembled
 constexpr int kMaxPcg = 600;          // iteration cap of the projected CG
 constexpr double kPcgTol = 1e-11;     // stop when res^T M^{-1} res <= tol^2 of its first value
@@ -167,14 +168,105 @@ __device__ void chain_solve(const AdjM& I, int i, const double* b, double* z, in
     }
 }
 
+// ---- grid-wide phases ------------------------------------------------------------
+//
+// The whole adjoint is one cooperative launch: every step below is a phase
+// over all instances of the batch, and the phases are separated by a grid
+// barrier.  A phase distributes its items over the grid in one of three ways:
+// one item per thread (assets, (period, factor) pairs, columns), one item per
+// warp (active rows, instances) or one item per block (instances).  Control
+// flow that reaches a barrier is the same in every block: it depends only on
+// values that all blocks read after the same barrier.
+
+// Barrier state in the workspace (zeroed by the host before the launch).
+struct GridSync {
+    unsigned int arrive;   // blocks arrived at the current barrier
+    unsigned int gen;      // barriers completed
+    int expired;           // a block's wait passed its limit
+    int pad;
+};
+
+constexpr long long kBarrierSpins = 1ll << 34;                   // polls of one wait
+constexpr unsigned long long kBarrierNs = 60ull * 1000000000ull;  // or 60 s of device time
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long device_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Every block arrives, the last one to arrive opens the next generation.  A
+// wait ends after kBarrierSpins polls or kBarrierNs of device time: it then
+// marks the launch expired and every block leaves at its next barrier.  A
+// cooperative launch keeps all blocks resident, so a wait expires only when
+// one phase runs longer than the limit (the one-block-per-instance Cholesky
+// of a very large active row set) or the device stops scheduling blocks.
+// Returns false once the launch expired.
+__device__ bool grid_barrier(GridSync* gs) {
+    __shared__ int ok_s;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned g = ld_acquire_u32(&gs->gen);
+        int ok = 1;
+        if (atomicAdd(&gs->arrive, 1u) == gridDim.x - 1) {
+            atomicExch(&gs->arrive, 0u);
+            st_release_u32(&gs->gen, g + 1);
+        } else {
+            const unsigned long long t0 = device_ns();
+            for (long long s = 0; ld_acquire_u32(&gs->gen) == g; ++s) {
+                if (s >= kBarrierSpins || ((s & 255) == 255 && device_ns() - t0 > kBarrierNs)) {
+                    atomicExch(&gs->expired, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok_s = ok && *(volatile int*)&gs->expired == 0;
+    }
+    __syncthreads();
+    __threadfence();
+    return ok_s != 0;
+}
+
+// fn(I, x) for every instance and every x < per(I) (one item per thread)
+template <class Per, class Fn>
+__device__ __forceinline__ void each_thread(const AdjM* insts, int count, int per_max, Per per, Fn fn) {
+    const long long total = (long long)count * per_max, stride = (long long)gridDim.x * blockDim.x;
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < total; v += stride) {
+        const AdjM& I = insts[v / per_max];
+        const int x = (int)(v % per_max);
+        if (x < per(I)) fn(I, x);
+    }
+}
+
+// fn(I, x, lane) for every instance and every x < per(I) (one item per warp)
+template <class Per, class Fn>
+__device__ __forceinline__ void each_warp(const AdjM* insts, int count, int per_max, Per per, Fn fn) {
+    const int lane = threadIdx.x & 31;
+    const long long total = (long long)count * per_max, stride = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long v = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < total; v += stride) {
+        const AdjM& I = insts[v / per_max];
+        const int x = (int)(v % per_max);
+        if (x < per(I)) fn(I, x, lane);
+    }
+}
+
 // ---- setup ------------------------------------------------------------------
 
 // Per asset: runs of periods joined by dead trades, fixed or free; trade
 // curvature; LDL^T of the chain's tridiagonal part.
-__global__ void __launch_bounds__(kMT) adjm_classify(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.y];
-    const int i = blockIdx.x * kMT + threadIdx.x;
-    if (i >= I.n) return;
+__device__ void classify_at(const AdjM& I, int i) {
     const int n = I.n, P = I.P;
     int p = 0;
     while (p < P) {
@@ -234,8 +326,7 @@ __global__ void __launch_bounds__(kMT) adjm_classify(const AdjM* __restrict__ in
 }
 
 // Active rows of every period (one block per instance) and the zeroed multipliers.
-__global__ void __launch_bounds__(kRT) adjm_rows(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.x];
+__device__ void rows_block(const AdjM& I) {
     __shared__ double red[kRT / 32];
     __shared__ int r_s;
     const int tid = threadIdx.x, n = I.n, P = I.P, m = I.m;
@@ -273,14 +364,13 @@ __global__ void __launch_bounds__(kRT) adjm_rows(const AdjM* __restrict__ insts)
         I.sc[0] = I.sc[1] = I.sc[2] = I.sc[3] = 0.0;
     }
     for (int a = tid; a < I.rmax; a += kRT) { I.nu[a] = 0; I.wv[a] = 0; I.ez[a] = 0; I.drop[a] = 0; }
+    __syncthreads();
 }
 
-// Columns c0 .. c0 + kNB - 1 of M^{-1} E^T (group space), one asset per thread.
-__global__ void __launch_bounds__(kMT) adjm_zcols(const AdjM* __restrict__ insts, int c0) {
-    const AdjM& I = insts[blockIdx.y];
-    const int i = blockIdx.x * kMT + threadIdx.x;
+// Columns c0 .. c0 + kNB - 1 of M^{-1} E^T (group space) for asset i.
+__device__ void zcols_at(const AdjM& I, int i, int c0) {
     const int r = I.flags[0];
-    if (i >= I.n || c0 >= r) return;
+    if (c0 >= r) return;
     const int n = I.n, P = I.P;
     for (int cc = 0; cc < kNB && c0 + cc < r; ++cc) {
         const int c = c0 + cc;
@@ -296,19 +386,17 @@ __global__ void __launch_bounds__(kMT) adjm_zcols(const AdjM* __restrict__ insts
     }
 }
 
-// C[a][c] = E_a . (M^{-1} E^T)_c for columns c0 .. c0 + kNB - 1: 8 rows x 32 columns per block.
-__global__ void __launch_bounds__(kRT) adjm_cfill(const AdjM* __restrict__ insts, int c0) {
-    const AdjM& I = insts[blockIdx.y];
+// C[a][c] = E_a . (M^{-1} E^T)_c for row a and the columns c0 + lane.
+__device__ void cfill_at(const AdjM& I, int a, int lane, int c0) {
     const int r = I.flags[0];
-    const int cc = threadIdx.x & 31, a = blockIdx.x * (kRT / 32) + (threadIdx.x >> 5);
-    const int c = c0 + cc;
+    const int c = c0 + lane;
     if (a >= r || c >= r) return;
     const int pa = I.rowp[a], ja = I.rowj[a], n = I.n;
     double acc = 0;
     for (int i = 0; i < n; ++i) {
         const int g = I.gfirst[(size_t)pa * n + i];
         if (g < 0) continue;
-        acc += erow(I, pa, ja, i) * I.Z[((size_t)g * n + i) * kNB + cc];
+        acc += erow(I, pa, ja, i) * I.Z[((size_t)g * n + i) * kNB + lane];
     }
     I.C[(size_t)a * I.rmax + c] = acc;
 }
@@ -317,8 +405,7 @@ __global__ void __launch_bounds__(kRT) adjm_cfill(const AdjM* __restrict__ insts
 // kDropRel of its original diagonal (or an empty row) is dependent on the rows
 // before it: its row and column of the factor are cleared, its pivot set to 1,
 // and it is marked dropped (its multiplier is 0).
-__global__ void __launch_bounds__(kRT) adjm_chol(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.x];
+__device__ void chol_block(const AdjM& I) {
     const int r = I.flags[0], ld = I.rmax;
     double* A = I.C;
     __shared__ int drop_s;
@@ -351,13 +438,9 @@ __global__ void __launch_bounds__(kRT) adjm_chol(const AdjM* __restrict__ insts)
     }
 }
 
-// Ci = C^{-1} column by column from the factor (one column per thread); the
-// rows and columns of dropped rows are zero.
-__global__ void __launch_bounds__(kMT) adjm_inverse(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.y];
+// Column c of Ci = C^{-1} from the factor; the rows and columns of dropped rows are zero.
+__device__ void inverse_at(const AdjM& I, int c) {
     const int r = I.flags[0], ld = I.rmax;
-    const int c = blockIdx.x * kMT + threadIdx.x;
-    if (c >= r) return;
     const double* L = I.C;
     double* X = I.Ci;
     for (int i = 0; i < r; ++i) {
@@ -379,11 +462,8 @@ __global__ void __launch_bounds__(kMT) adjm_inverse(const AdjM* __restrict__ ins
 
 // ---- projected conjugate gradients ---------------------------------------------
 
-// res = -S^T g, u = pd = 0, zz = M^{-1} res (one asset per thread)
-__global__ void __launch_bounds__(kMT) adjm_pcg_init(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.y];
-    const int i = blockIdx.x * kMT + threadIdx.x;
-    if (i >= I.n) return;
+// res = -S^T g, u = pd = 0, zz = M^{-1} res for asset i
+__device__ void pcg_init_at(const AdjM& I, int i) {
     const int n = I.n, P = I.P;
     for (int p = 0; p < P; ++p) {
         const size_t o = (size_t)p * n + i;
@@ -402,12 +482,9 @@ __global__ void __launch_bounds__(kMT) adjm_pcg_init(const AdjM* __restrict__ in
     chain_solve(I, i, I.res, I.zz, 1, 0);
 }
 
-// ez = E zz (one warp per active row)
-__global__ void __launch_bounds__(kRT) adjm_ez(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.y];
-    if (I.flags[1]) return;
-    const int a = blockIdx.x * (kRT / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (a >= I.flags[0]) return;
+// ez[a] = E_a zz (one warp per active row)
+__device__ void ez_at(const AdjM& I, int a, int lane) {
+    if (I.flags[1] || a >= I.flags[0]) return;
     const int pa = I.rowp[a], ja = I.rowj[a], n = I.n;
     double acc = 0;
     for (int i = lane; i < n; i += 32) {
@@ -418,13 +495,10 @@ __global__ void __launch_bounds__(kRT) adjm_ez(const AdjM* __restrict__ insts) {
     if (lane == 0) I.ez[a] = acc;
 }
 
-// w = C^{-1} ez; nu -= w (one warp per active row)
-__global__ void __launch_bounds__(kRT) adjm_w(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.y];
-    if (I.flags[1]) return;
+// w[a] = (C^{-1} ez)_a; nu[a] -= w[a] (one warp per active row)
+__device__ void w_at(const AdjM& I, int a, int lane) {
     const int r = I.flags[0];
-    const int a = blockIdx.x * (kRT / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (a >= r) return;
+    if (I.flags[1] || a >= r) return;
     double acc = 0;
     for (int c = lane; c < r; c += 32) acc += I.Ci[(size_t)a * I.rmax + c] * I.ez[c];
     acc = warp_sum(acc);
@@ -434,11 +508,9 @@ __global__ void __launch_bounds__(kRT) adjm_w(const AdjM* __restrict__ insts) {
     }
 }
 
-// res -= E^T w, zz = M^{-1} res, part = res . zz per asset
-__global__ void __launch_bounds__(kMT) adjm_update_res(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.y];
-    const int i = blockIdx.x * kMT + threadIdx.x;
-    if (i >= I.n || I.flags[1]) return;
+// res -= E^T w, zz = M^{-1} res, part = res . zz for asset i
+__device__ void update_res_at(const AdjM& I, int i) {
+    if (I.flags[1]) return;
     const int n = I.n, P = I.P;
     for (int p = 0; p < P; ++p) {
         const size_t o = (size_t)p * n + i;
@@ -458,10 +530,8 @@ __global__ void __launch_bounds__(kMT) adjm_update_res(const AdjM* __restrict__ 
 }
 
 // rz = sum(part): first value (init), else beta and the stopping test (one warp per instance)
-__global__ void adjm_rz(const AdjM* __restrict__ insts, int init) {
-    const AdjM& I = insts[blockIdx.x];
+__device__ void rz_at(const AdjM& I, int lane, int init) {
     if (I.flags[1]) return;
-    const int lane = threadIdx.x;
     double s = 0;
     for (int i = lane; i < I.n; i += 32) s += I.part[i];
     s = warp_sum(s);
@@ -481,11 +551,9 @@ __global__ void adjm_rz(const AdjM* __restrict__ insts, int init) {
     else if (I.flags[2] >= kMaxPcg) { I.flags[3] = 3; I.flags[1] = 1; }
 }
 
-// pd = -zz + beta pd
-__global__ void __launch_bounds__(kMT) adjm_pdir(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.y];
-    const int i = blockIdx.x * kMT + threadIdx.x;
-    if (i >= I.n || I.flags[1]) return;
+// pd = -zz + beta pd for asset i
+__device__ void pdir_at(const AdjM& I, int i) {
+    if (I.flags[1]) return;
     const double beta = I.sc[3];
     for (int p = 0; p < I.P; ++p) {
         const size_t o = (size_t)p * I.n + i;
@@ -494,13 +562,10 @@ __global__ void __launch_bounds__(kMT) adjm_pdir(const AdjM* __restrict__ insts)
 }
 
 // Uk[p][j] = sum_i v(p, i) F_{i,j} for v = pd (which 0), u (which 1) or, into
-// Uk2, the centred holdings x_p - w_T (which 2).  One (p, j) per thread.
-__global__ void __launch_bounds__(kMT) adjm_prodF(const AdjM* __restrict__ insts, int which) {
-    const AdjM& I = insts[blockIdx.y];
+// Uk2, the centred holdings x_p - w_T (which 2); e = p k + j.
+__device__ void prodF_at(const AdjM& I, int e, int which) {
     if (which == 0 && I.flags[1]) return;
-    const int e = blockIdx.x * kMT + threadIdx.x;
     const int n = I.n, k = I.k;
-    if (e >= I.P * k) return;
     const int p = e / k, j = e % k;
     double acc = 0;
     if (which == 2) {
@@ -517,13 +582,10 @@ __global__ void __launch_bounds__(kMT) adjm_prodF(const AdjM* __restrict__ insts
     }
 }
 
-// W[p] = 2 kappa Omega U[p] for (Uk -> Wk) (which 0) or (Uk2 -> Wk2) (which 1)
-__global__ void __launch_bounds__(kMT) adjm_omega(const AdjM* __restrict__ insts, int which, int in_pcg) {
-    const AdjM& I = insts[blockIdx.y];
+// W[p] = 2 kappa Omega U[p] for (Uk -> Wk) (which 0) or (Uk2 -> Wk2) (which 1); e = p k + j
+__device__ void omega_at(const AdjM& I, int e, int which, int in_pcg) {
     if (in_pcg && I.flags[1]) return;
-    const int e = blockIdx.x * kMT + threadIdx.x;
     const int k = I.k;
-    if (e >= I.P * k) return;
     const int p = e / k, j = e % k;
     const double* U = which == 0 ? I.Uk : I.Uk2;
     double* W = which == 0 ? I.Wk : I.Wk2;
@@ -537,11 +599,9 @@ __global__ void __launch_bounds__(kMT) adjm_omega(const AdjM* __restrict__ insts
     W[e] = 2.0 * I.kappa * acc;
 }
 
-// hp = H pd (group space) and part = pd . hp per asset
-__global__ void __launch_bounds__(kMT) adjm_hp(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.y];
-    const int i = blockIdx.x * kMT + threadIdx.x;
-    if (i >= I.n || I.flags[1]) return;
+// hp = H pd (group space) and part = pd . hp for asset i
+__device__ void hp_at(const AdjM& I, int i) {
+    if (I.flags[1]) return;
     const int n = I.n, P = I.P, k = I.k;
     double vprev = 0, vcur = gv(I, I.pd, 0, i);
     for (int p = 0; p < P; ++p) {
@@ -567,22 +627,19 @@ __global__ void __launch_bounds__(kMT) adjm_hp(const AdjM* __restrict__ insts) {
 }
 
 // alpha = rz / (pd . H pd) (one warp per instance)
-__global__ void adjm_alpha(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.x];
+__device__ void alpha_at(const AdjM& I, int lane) {
     if (I.flags[1]) return;
     double s = 0;
-    for (int i = threadIdx.x; i < I.n; i += 32) s += I.part[i];
+    for (int i = lane; i < I.n; i += 32) s += I.part[i];
     s = warp_sum(s);
-    if (threadIdx.x != 0) return;
+    if (lane != 0) return;
     if (!(s > 0) || !isfinite(s)) { I.flags[3] = 4; I.flags[1] = 1; return; }
     I.sc[2] = I.sc[0] / s;
 }
 
-// u += alpha pd, res += alpha hp, zz = M^{-1} res
-__global__ void __launch_bounds__(kMT) adjm_step(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.y];
-    const int i = blockIdx.x * kMT + threadIdx.x;
-    if (i >= I.n || I.flags[1]) return;
+// u += alpha pd, res += alpha hp, zz = M^{-1} res for asset i
+__device__ void step_at(const AdjM& I, int i) {
+    if (I.flags[1]) return;
     const double al = I.sc[2];
     for (int p = 0; p < I.P; ++p) {
         const size_t o = (size_t)p * I.n + i;
@@ -595,11 +652,8 @@ __global__ void __launch_bounds__(kMT) adjm_step(const AdjM* __restrict__ insts)
 
 // ---- assembly -------------------------------------------------------------------
 
-// Per asset: d alpha, d D (periods), d s, d q (trades), d w0, d w_T.
-__global__ void __launch_bounds__(kMT) adjm_grad_asset(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.y];
-    const int i = blockIdx.x * kMT + threadIdx.x;
-    if (i >= I.n) return;
+// Asset i: d alpha, d D (periods), d s, d q (trades), d w0, d w_T.
+__device__ void grad_asset_at(const AdjM& I, int i) {
     const int n = I.n, P = I.P, k = I.k, f64 = I.f64;
     const double kap = I.kappa, dexp = I.d;
     const double wTi = ldv(I.wT, i, f64);
@@ -647,13 +701,10 @@ __global__ void __launch_bounds__(kMT) adjm_grad_asset(const AdjM* __restrict__ 
     stv(I.dwT, i, dwT, f64);
 }
 
-// d F[i][j] = -sum_p (u_{p,i} Wk2[p][j] + (x_{p,i} - w_T,i) Wk[p][j])
-__global__ void __launch_bounds__(kMT) adjm_grad_F(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.y];
+// d F[i][j] = -sum_p (u_{p,i} Wk2[p][j] + (x_{p,i} - w_T,i) Wk[p][j]); e = i k + j
+__device__ void grad_F_at(const AdjM& I, int e) {
     if (!I.dF) return;
-    const int e = blockIdx.x * kMT + threadIdx.x;
-    const int n = I.n, k = I.k;
-    if (e >= n * k) return;
+    const int k = I.k;
     const int i = e / k, j = e % k;
     const double wTi = ldv(I.wT, i, I.f64);
     double acc = 0;
@@ -662,9 +713,111 @@ __global__ void __launch_bounds__(kMT) adjm_grad_F(const AdjM* __restrict__ inst
     stv(I.dF, e, -acc, I.f64);
 }
 
-__global__ void adjm_finish(const AdjM* __restrict__ insts) {
-    const AdjM& I = insts[blockIdx.x];
-    if (threadIdx.x == 0 && I.status_out) *I.status_out = I.flags[3];
+// Largest size of the batch for each item space of the phases.
+struct Extents {
+    int n;      // assets
+    int rows;   // rows_max = (T-1)(m+1)
+    int pk;     // (T-1) k
+    int nk;     // n k
+};
+
+// The adjoint of every instance: setup, the projected conjugate gradients
+// (converged instances take no further part; the loop ends when every
+// instance has stopped) and the assembly of the products.
+__global__ void __launch_bounds__(kRT) adjm_kernel(const AdjM* __restrict__ insts, int count, Extents ex,
+                                                   GridSync* gs) {
+    auto nA = [](const AdjM& I) { return I.n; };
+    auto nR = [](const AdjM& I) { return I.rmax; };
+    auto nPK = [](const AdjM& I) { return I.P * I.k; };
+    auto nNK = [](const AdjM& I) { return I.n * I.k; };
+    auto one = [](const AdjM&) { return 1; };
+    __shared__ int flag_s;
+
+    each_thread(insts, count, ex.n, nA, [](const AdjM& I, int i) { classify_at(I, i); });
+    if (!grid_barrier(gs)) goto expired;
+    for (int t = blockIdx.x; t < count; t += gridDim.x) rows_block(insts[t]);
+    if (!grid_barrier(gs)) goto expired;
+    {
+        // the passes over the columns of M^{-1} E^T cover the largest active row count
+        int rmax_act = 0;
+        for (int t = 0; t < count; ++t) rmax_act = max(rmax_act, *(volatile int*)&insts[t].flags[0]);
+        for (int c0 = 0; c0 < rmax_act; c0 += kNB) {
+            each_thread(insts, count, ex.n, nA, [c0](const AdjM& I, int i) { zcols_at(I, i, c0); });
+            if (!grid_barrier(gs)) goto expired;
+            each_warp(insts, count, ex.rows, nR, [c0](const AdjM& I, int a, int lane) { cfill_at(I, a, lane, c0); });
+            if (!grid_barrier(gs)) goto expired;
+        }
+    }
+    for (int t = blockIdx.x; t < count; t += gridDim.x) chol_block(insts[t]);
+    if (!grid_barrier(gs)) goto expired;
+    each_thread(insts, count, ex.rows, nR, [](const AdjM& I, int c) { if (c < I.flags[0]) inverse_at(I, c); });
+    if (!grid_barrier(gs)) goto expired;
+
+    // first projection: res = -S^T g, then the component in null(E)
+    each_thread(insts, count, ex.n, nA, [](const AdjM& I, int i) { pcg_init_at(I, i); });
+    if (!grid_barrier(gs)) goto expired;
+    each_warp(insts, count, ex.rows, nR, [](const AdjM& I, int a, int lane) { ez_at(I, a, lane); });
+    if (!grid_barrier(gs)) goto expired;
+    each_warp(insts, count, ex.rows, nR, [](const AdjM& I, int a, int lane) { w_at(I, a, lane); });
+    if (!grid_barrier(gs)) goto expired;
+    each_thread(insts, count, ex.n, nA, [](const AdjM& I, int i) { update_res_at(I, i); });
+    if (!grid_barrier(gs)) goto expired;
+    each_warp(insts, count, 1, one, [](const AdjM& I, int, int lane) { rz_at(I, lane, 1); });
+    if (!grid_barrier(gs)) goto expired;
+    each_thread(insts, count, ex.n, nA, [](const AdjM& I, int i) { pdir_at(I, i); });
+    if (!grid_barrier(gs)) goto expired;
+
+    for (int it = 0; it < kMaxPcg; ++it) {
+        // every block reads the same stop flags here: they change only in the
+        // alpha and rz phases, each followed by a barrier
+        if (threadIdx.x == 0) {
+            int live = 0;
+            for (int t = 0; t < count && !live; ++t) live = *(volatile int*)&insts[t].flags[1] == 0;
+            flag_s = live;
+        }
+        __syncthreads();
+        const int live = flag_s;
+        __syncthreads();
+        if (!live) break;
+        each_thread(insts, count, ex.pk, nPK, [](const AdjM& I, int e) { prodF_at(I, e, 0); });
+        if (!grid_barrier(gs)) goto expired;
+        each_thread(insts, count, ex.pk, nPK, [](const AdjM& I, int e) { omega_at(I, e, 0, 1); });
+        if (!grid_barrier(gs)) goto expired;
+        each_thread(insts, count, ex.n, nA, [](const AdjM& I, int i) { hp_at(I, i); });
+        if (!grid_barrier(gs)) goto expired;
+        each_warp(insts, count, 1, one, [](const AdjM& I, int, int lane) { alpha_at(I, lane); });
+        if (!grid_barrier(gs)) goto expired;
+        each_thread(insts, count, ex.n, nA, [](const AdjM& I, int i) { step_at(I, i); });
+        if (!grid_barrier(gs)) goto expired;
+        each_warp(insts, count, ex.rows, nR, [](const AdjM& I, int a, int lane) { ez_at(I, a, lane); });
+        if (!grid_barrier(gs)) goto expired;
+        each_warp(insts, count, ex.rows, nR, [](const AdjM& I, int a, int lane) { w_at(I, a, lane); });
+        if (!grid_barrier(gs)) goto expired;
+        each_thread(insts, count, ex.n, nA, [](const AdjM& I, int i) { update_res_at(I, i); });
+        if (!grid_barrier(gs)) goto expired;
+        each_warp(insts, count, 1, one, [](const AdjM& I, int, int lane) { rz_at(I, lane, 0); });
+        if (!grid_barrier(gs)) goto expired;
+        each_thread(insts, count, ex.n, nA, [](const AdjM& I, int i) { pdir_at(I, i); });
+        if (!grid_barrier(gs)) goto expired;
+    }
+
+    // assembly: F^T u and F^T (x - w_T), their Omega products, the gradients
+    each_thread(insts, count, ex.pk, nPK, [](const AdjM& I, int e) { prodF_at(I, e, 1); prodF_at(I, e, 2); });
+    if (!grid_barrier(gs)) goto expired;
+    each_thread(insts, count, ex.pk, nPK, [](const AdjM& I, int e) { omega_at(I, e, 0, 0); omega_at(I, e, 1, 0); });
+    if (!grid_barrier(gs)) goto expired;
+    each_thread(insts, count, ex.n, nA, [](const AdjM& I, int i) { grad_asset_at(I, i); });
+    each_thread(insts, count, ex.nk, nNK, [](const AdjM& I, int e) { grad_F_at(I, e); });
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x)
+        if (insts[t].status_out) *insts[t].status_out = insts[t].flags[3];
+    return;
+
+expired:
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+        insts[t].flags[3] = 5;
+        insts[t].flags[1] = 1;
+        if (insts[t].status_out) *insts[t].status_out = 5;
+    }
 }
 
 inline size_t a256(size_t x) { return (x + 255) / 256 * 256; }
@@ -751,7 +904,7 @@ extern "C" {
 
 size_t ff_backward_multi_workspace_size(const ff_problem* probs, int count) {
     if (!probs || count < 1) return 0;
-    size_t b = ff::a256((size_t)count * sizeof(ff::AdjM));
+    size_t b = ff::a256((size_t)count * sizeof(ff::AdjM)) + ff::a256(sizeof(ff::GridSync));
     for (int t = 0; t < count; ++t) {
         const ff_problem* p = &probs[t];
         if (p->T < 2 || p->n < 1 || p->k < 1 || p->m < 0) return 0;
@@ -779,57 +932,36 @@ int ff_backward_multi_batch(const ff_problem* probs, int count, const void* cons
     }
     const size_t need = ff_backward_multi_workspace_size(probs, count);
     if (!ws || ((uintptr_t)ws % 256) != 0 || ws_bytes < need) return FF_ERR_WORKSPACE;
+    int dev = 0, coop = 0, sms = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ff::adjm_kernel, ff::kRT, 0) != cudaSuccess)
+        return FF_ERR_CUDA;
+    if (!coop || occ < 1 || sms < 1) return FF_ERR_UNSUPPORTED;
     unsigned char* base = (unsigned char*)ws;
-    unsigned char* cur = base + ff::a256((size_t)count * sizeof(ff::AdjM));
+    ff::GridSync* gs = (ff::GridSync*)(base + ff::a256((size_t)count * sizeof(ff::AdjM)));
+    unsigned char* cur = (unsigned char*)gs + ff::a256(sizeof(ff::GridSync));
     std::vector<ff::AdjM> table(count);
     for (int t = 0; t < count; ++t)
         table[t] = ff::carve_multi(&probs[t], w[t], yA ? yA[t] : nullptr, yD[t], grad_w[t], &out[t], cur,
                                    status_dev ? status_dev + t : nullptr);
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMemcpyAsync(base, table.data(), (size_t)count * sizeof(ff::AdjM), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemsetAsync(gs, 0, sizeof(ff::GridSync), st) != cudaSuccess)
+        return FF_ERR_CUDA;
+    // one block per SM, more (up to the occupancy, at most 4) when the
+    // per-asset phases have more assets than one block per SM has threads
+    const long long items = (long long)count * nmax;
+    int per_sm = (int)std::min<long long>(4, (items + (long long)sms * ff::kRT - 1) / ((long long)sms * ff::kRT));
+    per_sm = std::max(1, std::min(per_sm, occ));
+    const ff::AdjM* T = (const ff::AdjM*)base;
+    ff::Extents ex{nmax, rmax, pkmax, nkmax};
+    void* args[] = {(void*)&T, (void*)&count, (void*)&ex, (void*)&gs};
+    if (cudaLaunchCooperativeKernel((const void*)ff::adjm_kernel, dim3(sms * per_sm), dim3(ff::kRT), args, 0, st) !=
         cudaSuccess)
         return FF_ERR_CUDA;
-    const ff::AdjM* T = (const ff::AdjM*)base;
-    using ff::kMT;
-    using ff::kRT;
-    const dim3 gA((nmax + kMT - 1) / kMT, count);                 // one asset per thread
-    const dim3 gR((rmax + kRT / 32 - 1) / (kRT / 32), count);     // one row per warp
-    const dim3 gC((rmax + kMT - 1) / kMT, count);                 // one column per thread
-    const dim3 gPK((pkmax + kMT - 1) / kMT, count);               // one (period, factor) per thread
-    const dim3 gNK((nkmax + kMT - 1) / kMT, count);               // one (asset, factor) per thread
-    ff::adjm_classify<<<gA, kMT, 0, st>>>(T);
-    ff::adjm_rows<<<count, kRT, 0, st>>>(T);
-    for (int c0 = 0; c0 < rmax; c0 += ff::kNB) {
-        ff::adjm_zcols<<<gA, kMT, 0, st>>>(T, c0);
-        ff::adjm_cfill<<<gR, kRT, 0, st>>>(T, c0);
-    }
-    ff::adjm_chol<<<count, kRT, 0, st>>>(T);
-    ff::adjm_inverse<<<gC, kMT, 0, st>>>(T);
-    ff::adjm_pcg_init<<<gA, kMT, 0, st>>>(T);
-    ff::adjm_ez<<<gR, kRT, 0, st>>>(T);
-    ff::adjm_w<<<gR, kRT, 0, st>>>(T);
-    ff::adjm_update_res<<<gA, kMT, 0, st>>>(T);
-    ff::adjm_rz<<<count, 32, 0, st>>>(T, 1);
-    ff::adjm_pdir<<<gA, kMT, 0, st>>>(T);
-    for (int it = 0; it < ff::kMaxPcg; ++it) {
-        ff::adjm_prodF<<<gPK, kMT, 0, st>>>(T, 0);
-        ff::adjm_omega<<<gPK, kMT, 0, st>>>(T, 0, 1);
-        ff::adjm_hp<<<gA, kMT, 0, st>>>(T);
-        ff::adjm_alpha<<<count, 32, 0, st>>>(T);
-        ff::adjm_step<<<gA, kMT, 0, st>>>(T);
-        ff::adjm_ez<<<gR, kRT, 0, st>>>(T);
-        ff::adjm_w<<<gR, kRT, 0, st>>>(T);
-        ff::adjm_update_res<<<gA, kMT, 0, st>>>(T);
-        ff::adjm_rz<<<count, 32, 0, st>>>(T, 0);
-        ff::adjm_pdir<<<gA, kMT, 0, st>>>(T);
-    }
-    ff::adjm_prodF<<<gPK, kMT, 0, st>>>(T, 1);
-    ff::adjm_omega<<<gPK, kMT, 0, st>>>(T, 0, 0);
-    ff::adjm_prodF<<<gPK, kMT, 0, st>>>(T, 2);
-    ff::adjm_omega<<<gPK, kMT, 0, st>>>(T, 1, 0);
-    ff::adjm_grad_asset<<<gA, kMT, 0, st>>>(T);
-    ff::adjm_grad_F<<<gNK, kMT, 0, st>>>(T);
-    ff::adjm_finish<<<count, 32, 0, st>>>(T);
     if (cudaGetLastError() != cudaSuccess) return FF_ERR_CUDA;
     return FF_OK;
 }

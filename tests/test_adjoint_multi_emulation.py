@@ -1,13 +1,13 @@
 """Serial CPU transcription of the multi-period adjoint kernels
 (csrc/ff_adjoint_multi.cu), checked against the oracle's implicit derivative.
 
-Each function below mirrors one kernel (adjm_classify, adjm_rows,
-adjm_zcols, adjm_cfill, adjm_chol, adjm_inverse, adjm_pcg_init, adjm_ez,
-adjm_w, adjm_update_res, adjm_rz, adjm_pdir, adjm_prodF, adjm_omega, adjm_hp,
-adjm_alpha, adjm_step, adjm_grad_asset, adjm_grad_F) with the same storage
-(period-major P x n group-space vectors at each group's first period, the
-kNB-column panel of M^-1 E^T, row-major C with leading dimension rmax), the
-same index arithmetic and the same launch order; threads become loops.  Every
+Each function below mirrors one phase of the cooperative kernel adjm_kernel
+(classify, rows, zcols, cfill, chol, inverse, pcg_init, ez, w, update_res,
+rz, pdir, prodF, omega, hp, alpha, step, grad_asset, grad_F) with the same
+storage (period-major P x n group-space vectors at each group's first
+period, the kNB-column panel of M^-1 E^T, row-major C with leading dimension
+rmax), the same index arithmetic and the same phase order; threads become
+loops.  Every
 workspace buffer starts as NaN and is bounds-checked (a negative or
 out-of-range index raises), so a read before a write or an index outside a
 buffer fails here, on the CPU.  This checks the GPU algorithm and its

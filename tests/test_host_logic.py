@@ -132,8 +132,8 @@ def test_batchrunner_backward_dispatch(monkeypatch):
     assert single["status"] == base and multi["status"] == base + 8
     br._bstatus_sub.copy_(torch.tensor([10, 12, 11, 13], dtype=torch.int32))
     assert br.bstatus.tolist() == [10, 11, 12, 13]
-    # one single-period launch; the multi-period sequence for rmax = 3 (4 + 1) = 15 rows
-    assert br.backward_launches() == 1 + (2 + 2 * 1 + 2 + 6 + 6000 + 7)
+    # one single-period launch and one cooperative multi-period launch
+    assert br.backward_launches() == 2
 
 
 def test_multi_autograd_rejects_a_single_period_shape():
