@@ -220,6 +220,31 @@ int ff_solve_batch(const ff_problem* probs, int count, const ff_options* o, void
                    ff_result* result_dev, void* const* w_out, void* const* yA_out, void* const* yD_out,
                    void* stream);
 
+/* Workspace bytes of ff_solve_joint_batch for these instances (host only; 0 if
+ * an instance is not single-period or a size is invalid).  Per instance about
+ * 8 n (k + m + 12) bytes: FP64 copies of F (transposed) and A, and the state. */
+size_t ff_joint_workspace_size(const ff_problem* probs, int count);
+
+/* The joint primal prox variant of the single-period solve (Eqs. 1-3): the
+ * trading cost and the budget set of Eq. 3 form one primal prox,
+ *   prox(v)_i = argmin_w 0.5 (w - v_i)^2 + tau phi_i(w - w0_i) + mu |w|,
+ * with the budget multiplier mu found by a safeguarded Newton iteration, so the
+ * only multiplier of the iteration is y_A; the steps, the reflected Halpern
+ * scheme, the restarts and the relative KKT test (with the trade multiplier
+ * recovered from the prox's optimality condition) are those of ff_solve_batch.
+ * FP64 throughout, one CTA per instance; o->precision must be FF_PREC_F64
+ * (else FF_ERR_UNSUPPORTED), every instance single-period (T = 0) with k <= 256
+ * and m <= 256 (else FF_ERR_UNSUPPORTED).  warm_start, cluster_size, cta_work,
+ * max_teams, stall_checks, round_panels_bf16, panel_l2_keep, primal_weight and
+ * the test hook have no effect.  Arguments and outputs as ff_solve_batch
+ * (yD_out receives the recovered trade multiplier); ff_result.threshold_rounds
+ * counts the evaluations of ||w(mu)||_1.  ws: ff_joint_workspace_size bytes,
+ * 256-byte aligned.  Asynchronous on `stream` (one launch after a host-to-device
+ * copy of the instance table); FF_OK or an FF_ERR_* code. */
+int ff_solve_joint_batch(const ff_problem* probs, int count, const ff_options* o, void* ws, size_t ws_bytes,
+                         ff_result* result_dev, void* const* w_out, void* const* yA_out, void* const* yD_out,
+                         void* stream);
+
 /* Size of the library-owned workspace used by ff_solve_single_static (32 MiB). */
 #define FF_STATIC_WORKSPACE_BYTES (32u * 1024u * 1024u)
 

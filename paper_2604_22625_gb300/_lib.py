@@ -85,7 +85,8 @@ EXPORTS = ("ff_default_options", "ff_workspace_size", "ff_solve_single", "ff_sol
            "ff_solve_batch", "ff_status_string", "ff_version", "ff_last_error",
            "ff_solve_single_static", "ff_batch_plan", "ff_backward", "ff_backward_single", "ff_backward_workspace_size",
            "ff_backward_batch", "ff_backward_batch_workspace_size", "ff_backward_multi_batch",
-           "ff_backward_multi_workspace_size", "ff_risk_workspace_size", "ff_risk_estimate", "ff_risk_last_error")
+           "ff_backward_multi_workspace_size", "ff_risk_workspace_size", "ff_risk_estimate", "ff_risk_last_error",
+           "ff_joint_workspace_size", "ff_solve_joint_batch")
 
 _lib = None
 
@@ -134,6 +135,10 @@ def load(path: str = LIB_PATH) -> C.CDLL:
                                    C.c_size_t, C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
                                    C.POINTER(C.c_void_p), C.c_void_p]
     lib.ff_solve_batch.restype = C.c_int
+    lib.ff_joint_workspace_size.argtypes = [C.POINTER(ff_problem), C.c_int]
+    lib.ff_joint_workspace_size.restype = C.c_size_t
+    lib.ff_solve_joint_batch.argtypes = lib.ff_solve_batch.argtypes
+    lib.ff_solve_joint_batch.restype = C.c_int
     lib.ff_status_string.argtypes = [C.c_int]
     lib.ff_status_string.restype = C.c_char_p
     lib.ff_last_error.argtypes = []
@@ -220,6 +225,19 @@ def ff_solve_batch(probs, count: int, opts: ff_options, ws: int, ws_bytes: int, 
     yd = (C.c_void_p * count)(*yD_ptrs) if yD_ptrs is not None else None
     return int(load().ff_solve_batch(probs, count, C.byref(opts), C.c_void_p(ws), ws_bytes, C.c_void_p(res),
                                      arr, ya, yd, C.c_void_p(stream or None)))
+
+
+def ff_joint_workspace_size(probs, count: int) -> int:
+    return int(load().ff_joint_workspace_size(probs, count))
+
+
+def ff_solve_joint_batch(probs, count: int, opts: ff_options, ws: int, ws_bytes: int, res: int, w_ptrs,
+                         stream: int = 0, yA_ptrs=None, yD_ptrs=None) -> int:
+    arr = (C.c_void_p * count)(*w_ptrs)
+    ya = (C.c_void_p * count)(*yA_ptrs) if yA_ptrs is not None else None
+    yd = (C.c_void_p * count)(*yD_ptrs) if yD_ptrs is not None else None
+    return int(load().ff_solve_joint_batch(probs, count, C.byref(opts), C.c_void_p(ws), ws_bytes,
+                                           C.c_void_p(res), arr, ya, yd, C.c_void_p(stream or None)))
 
 
 def ff_backward_batch_workspace_size(probs, count: int) -> int:

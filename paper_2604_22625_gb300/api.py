@@ -477,6 +477,39 @@ def solve_batch(problems: Sequence, precision: str = "bf16", device: str = "cuda
     return br.portfolios(), br.results()
 
 
+def solve_joint(problems: Sequence, device: str = "cuda", stream: Optional[torch.cuda.Stream] = None,
+                **opt_kw) -> List[Solution]:
+    """Single-period instances through the joint primal prox variant
+    (ff_solve_joint_batch: trading cost and budget set in one primal prox, FP64,
+    one CTA per instance); returns host copies of w, y_A, the recovered trade
+    multiplier y_D and the result record of every instance."""
+    probs = list(problems)
+    if any(int(getattr(p, "T", 0)) >= 2 for p in probs):
+        raise ValueError("the joint prox variant solves single-period instances only")
+    dps = [to_device(p, dtype=torch.float64, device=device) for p in probs]
+    count = len(dps)
+    structs = (L.ff_problem * count)(*[d.struct for d in dps])
+    opts = options("f64", **opt_kw)
+    nb = L.ff_joint_workspace_size(structs, count)
+    if nb == 0:
+        raise ValueError("invalid problem for the joint prox variant")
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device=device)
+    base = (ws.data_ptr() + 255) // 256 * 256
+    res = torch.zeros(count * L.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=device)
+    ws_ = [torch.empty(d.n, dtype=torch.float64, device=device) for d in dps]
+    ya = [torch.empty(max(d.m, 1), dtype=torch.float64, device=device) for d in dps]
+    yd = [torch.empty(d.n, dtype=torch.float64, device=device) for d in dps]
+    s = stream if stream is not None else torch.cuda.current_stream(device)
+    rc = L.ff_solve_joint_batch(structs, count, opts, base, nb, res.data_ptr(), [t.data_ptr() for t in ws_],
+                                s.cuda_stream, [t.data_ptr() for t in ya], [t.data_ptr() for t in yd])
+    if rc != L.FF_OK:
+        raise RuntimeError(f"ff_solve_joint_batch: {L.ff_status_string(rc)} ({rc}) {L.ff_last_error()}")
+    s.synchronize()
+    recs = res.cpu().numpy().view(L.RESULT_DTYPE)
+    return [Solution(w.cpu().numpy(), a[:d.m].cpu().numpy(), y.cpu().numpy(), _info(r))
+            for w, a, y, d, r in zip(ws_, ya, yd, dps, recs)]
+
+
 @dataclass
 class RiskModels:
     """Device results of ``estimate_risk`` for ``count`` windows."""

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libflashfolio.so")
-SOURCES = ["ff_api.cu", "ff_solver.cu", "ff_adjoint.cu", "ff_adjoint_multi.cu", "ff_risk.cu"]
+SOURCES = ["ff_api.cu", "ff_solver.cu", "ff_adjoint.cu", "ff_adjoint_multi.cu", "ff_risk.cu", "ff_joint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -703,6 +703,27 @@ void ff_default_options(ff_options* o) {
     if (o) ff::fill_defaults(o);
 }
 
+size_t ff_joint_workspace_size(const ff_problem* probs, int count) {
+    if (!probs || count < 1) return 0;
+    for (int t = 0; t < count; ++t)
+        if (!ff::valid_problem(&probs[t])) return 0;
+    return ff::joint_workspace_bytes(probs, count);
+}
+
+int ff_solve_joint_batch(const ff_problem* probs, int count, const ff_options* o_in, void* ws, size_t ws_bytes,
+                         ff_result* result_dev, void* const* w_out, void* const* yA_out, void* const* yD_out,
+                         void* stream) {
+    if (!probs || count < 1 || count > 65535 || !result_dev || !w_out) return FF_ERR_INVALID_ARG;
+    ff_options o;
+    if (o_in) o = *o_in; else ff::fill_defaults(&o);
+    if (!ff::valid_options(o)) return FF_ERR_INVALID_ARG;
+    if (o.precision != FF_PREC_F64) return FF_ERR_UNSUPPORTED;
+    for (int t = 0; t < count; ++t)
+        if (!ff::valid_problem(&probs[t])) return FF_ERR_INVALID_ARG;
+    return ff::joint_solve(probs, count, ff::make_params(o), ws, ws_bytes, result_dev, w_out, yA_out, yD_out,
+                           (cudaStream_t)stream);
+}
+
 size_t ff_workspace_size(const ff_problem* probs, int count, const ff_options* o_in) {
     if (!probs || count < 1) return 0;
     ff_options o;

@@ -132,6 +132,13 @@ __host__ __device__ inline int rep_doubles(int P, int k, int m) {
 int choose_tile(int P, int n, int k, int m, int omega_diag, size_t matvec_size, size_t panel_size, int* vcap,
                 int* rep_glob);
 
+// Joint primal prox variant (single period, FP64): workspace bytes (0 if an
+// instance is not single-period or a size is invalid) and the launch of one
+// CTA per instance; FF_ERR_UNSUPPORTED beyond 256 factors or exposure rows.
+size_t joint_workspace_bytes(const ff_problem* probs, int count);
+int joint_solve(const ff_problem* probs, int count, const Params& prm, void* ws, size_t ws_bytes, ff_result* res,
+                void* const* w_out, void* const* yA_out, void* const* yD_out, cudaStream_t st);
+
 // Launch the team kernel over `count` instances (insts is a device array).
 // G = CTAs per instance (cluster size), nteams = concurrent teams; single =
 // every instance is single-period (the variant built for P = 1).

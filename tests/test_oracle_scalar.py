@@ -100,3 +100,65 @@ def test_conjugate_matches_supremum(d):
         assert abs(float(cost_conjugate(y, c1, c2, d)) - sup) <= 1e-9 * max(1.0, abs(sup)) + 1e-12
     assert cost_conjugate(5e-4, 1e-3, 1e-2, 1.5) == 0.0
     assert np.isinf(cost_conjugate(2e-3, 1e-3, 0.0, 1.5))
+
+
+# ---- joint primal prox: trading cost of Eq. 1 and budget set of Eq. 3 together ----
+
+from oracle.prox import prox_joint, prox_joint_coord  # noqa: E402
+
+
+@pytest.mark.parametrize("d", [1.3, 1.5, 2.0])
+def test_joint_coordinate_matches_direct_minimisation(d):
+    """The coordinate problem 0.5 (w - v)^2 + gamma phi(w - a) + mu |w| (two
+    kinks, at 0 and at a) against golden-section search of its objective."""
+    rng = np.random.default_rng(11)
+    for _ in range(300):
+        v, a = rng.normal(0, 0.05), rng.normal(0, 0.02)
+        gamma, mu = 10 ** rng.uniform(-1, 1), rng.uniform(0, 0.05)
+        c1, c2 = rng.uniform(0, 5e-3), rng.uniform(0, 5e-2)
+        obj = lambda w: 0.5 * (w - v) ** 2 + gamma * (c1 * abs(w - a) + c2 * abs(w - a) ** d) + mu * abs(w)
+        w = float(prox_joint_coord(v, a, mu, gamma, c1, c2, d))
+        ws = _golden_min(obj, -abs(v) - abs(a) - 1e-2, abs(v) + abs(a) + 1e-2, iters=300)
+        assert obj(w) <= obj(ws) + 1e-15
+        assert abs(w - ws) <= 1e-6
+
+
+def test_joint_prox_reduces_to_projection_and_to_separable_prox():
+    """No cost (c1 = c2 = 0): the projection onto the budget set, with mu the
+    projection's threshold; a ball that does not bind: a + prox_cost(v - a)."""
+    rng = np.random.default_rng(12)
+    v = rng.normal(0, 0.1, 40)
+    a = rng.normal(0, 0.02, 40)
+    w, mu = prox_joint(v, a, 1.0, 0.0, 0.0, 1.5)
+    assert np.max(np.abs(w - project_l1(v))) <= 1e-15
+    assert abs(mu - l1_threshold(v)) <= 1e-14
+    c1, c2 = rng.uniform(0, 2e-3, 40), rng.uniform(0, 2e-2, 40)
+    w, mu = prox_joint(v, a, 0.5, c1, c2, 1.5, radius=100.0)
+    assert mu == 0.0
+    assert np.max(np.abs(w - (a + prox_cost(v - a, 0.5, c1, c2, 1.5)))) <= 1e-15
+
+
+def test_joint_prox_brute_force_2d():
+    """Two assets: the joint prox against a grid search over the ball, and its
+    optimality conditions (a subgradient of every term balancing w - v, the
+    budget tight when mu > 0)."""
+    rng = np.random.default_rng(13)
+    d = 1.5
+    g = np.linspace(-1.0, 1.0, 2001)
+    W1, W2 = np.meshgrid(g, g, indexing="ij")
+    inside = np.abs(W1) + np.abs(W2) <= 1.0
+    for _ in range(6):
+        v = rng.normal(0, 0.8, 2)
+        a = rng.normal(0, 0.3, 2)
+        gamma, c1, c2 = 0.5, rng.uniform(0.05, 0.3, 2), rng.uniform(0.05, 0.3, 2)
+        w, mu = prox_joint(v, a, gamma, c1, c2, d)
+        cost = lambda x1, x2: (0.5 * ((x1 - v[0]) ** 2 + (x2 - v[1]) ** 2)
+                               + gamma * (c1[0] * np.abs(x1 - a[0]) + c2[0] * np.abs(x1 - a[0]) ** d
+                                          + c1[1] * np.abs(x2 - a[1]) + c2[1] * np.abs(x2 - a[1]) ** d))
+        grid = np.where(inside, cost(W1, W2), np.inf)
+        best = np.unravel_index(np.argmin(grid), grid.shape)
+        assert np.abs(w).sum() <= 1.0 + 1e-12
+        assert float(cost(w[0], w[1])) <= float(grid[best]) + 1e-12
+        assert np.max(np.abs(w - np.array([g[best[0]], g[best[1]]]))) <= 2e-3
+        if mu > 0:
+            assert abs(np.abs(w).sum() - 1.0) <= 1e-12
