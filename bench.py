@@ -51,8 +51,9 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="batch",
                     choices=["batch", "single_large", "multi", "single_small", "batch_profile", "multi_profile",
-                             "diff", "risk", "paper_grid"])
+                             "diff", "risk", "paper_grid", "joint"])
     ap.add_argument("--grid-n", type=int, default=2000, help="paper_grid: assets per instance")
+    ap.add_argument("--joint-count", type=int, default=64, help="joint: single-period instances compared")
     ap.add_argument("--grid-dates", type=int, default=21, help="paper_grid: instances (dates) per setting")
     ap.add_argument("--eta", default="literal", choices=["literal", "inverted"], help="paper_grid: reading "
                     "of the intraday cost profile")
@@ -887,10 +888,109 @@ def run_paper_grid(args):
     return 0
 
 
+def run_joint(args):
+    """The joint primal prox variant (ff_solve_joint_batch) against the plain
+    split (ff_solve_batch) on the same single-period instances of the batch
+    workload, both in FP64 and to the same tolerance: iterations per instance,
+    device time per call (CUDA events on the launching stream), agreement of
+    the two solutions, and the oracle on a sample."""
+    import torch
+    from paper_2604_22625_gb300 import api
+    from paper_2604_22625_gb300 import _lib as L
+    from paper_2604_22625_gb300 import synthetic as S
+    from paper_2604_22625_gb300.build import build
+    build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    singles = [p for p in S.config_batch(seed=rank_seed(3, 0)) if int(p.T) < 2]
+    step = max(1, len(singles) // args.joint_count)
+    probs = singles[::step][:args.joint_count]
+    count = len(probs)
+    stream = torch.cuda.current_stream(dev)
+    # joint arm: device problems, workspace and outputs set up once
+    dps = [api.to_device(p, dtype=torch.float64, device=str(dev)) for p in probs]
+    structs = (L.ff_problem * count)(*[d.struct for d in dps])
+    opts = api.options("f64", tol=args.tol, time_limit=360.0)
+    nb = L.ff_joint_workspace_size(structs, count)
+    ws = torch.empty(nb, dtype=torch.uint8, device=dev)
+    res = torch.zeros(count * L.RESULT_DTYPE.itemsize, dtype=torch.uint8, device=dev)
+    wj = [torch.empty(d.n, dtype=torch.float64, device=dev) for d in dps]
+    yaj = [torch.empty(max(d.m, 1), dtype=torch.float64, device=dev) for d in dps]
+    ydj = [torch.empty(d.n, dtype=torch.float64, device=dev) for d in dps]
+
+    def joint_call():
+        rc = L.ff_solve_joint_batch(structs, count, opts, ws.data_ptr(), nb, res.data_ptr(),
+                                    [t.data_ptr() for t in wj], stream.cuda_stream,
+                                    [t.data_ptr() for t in yaj], [t.data_ptr() for t in ydj])
+        if rc != L.FF_OK:
+            raise RuntimeError(f"ff_solve_joint_batch: {L.ff_status_string(rc)} {L.ff_last_error()}")
+
+    plain = api.BatchRunner(probs, precision="f64", device=str(dev), duals=True, tol=args.tol, time_limit=360.0)
+
+    def timed(fn, steps):
+        ms = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    for _ in range(max(1, args.warmup)):
+        joint_call()
+        plain.run(stream)
+    torch.cuda.synchronize(dev)
+    steps = max(1, args.steps)
+    ms_joint = timed(joint_call, steps)
+    ms_plain = timed(lambda: plain.run(stream), steps)
+    jinfo = [api._info(r) for r in res.cpu().numpy().view(L.RESULT_DTYPE)]
+    pinfo = plain.results()
+    it_j = np.array([i["iterations"] for i in jinfo], dtype=np.float64)
+    it_p = np.array([i["iterations"] for i in pinfo], dtype=np.float64)
+    ok_j = sum(1 for i in jinfo if i["status"] == 0 and i["rel_kkt"] <= args.tol)
+    ok_p = sum(1 for i in pinfo if i["status"] == 0 and i["rel_kkt"] <= args.tol)
+    wp = plain.portfolios()
+    diff = max(float(np.max(np.abs(wj[t].cpu().numpy() - np.asarray(wp[t]).ravel()))) for t in range(count))
+    # the oracle on the smallest, the median and the largest instances
+    order = sorted(range(count), key=lambda t: probs[t].F.shape[0])
+    picks = sorted(set([order[0], order[count // 2], order[-1]]))
+    pool = spawn_pool(len(picks))
+    tasks = [(probs[t].tag, probs[t], "f64", wj[t].cpu().numpy(), yaj[t][:dps[t].m].cpu().numpy(),
+              ydj[t].cpu().numpy()) for t in picks]
+    checks = pool.map(_oracle_check_one, tasks)
+    pool.close()
+    pool.join()
+    mj, mp = statistics.mean(ms_joint), statistics.mean(ms_plain)
+    line = {"metric": "joint primal prox vs plain split (single-period, FP64): solves/s", "unit": "solves/s",
+            "value": ok_j / (mj / 1e3), "plain_value": ok_p / (mp / 1e3), "higher_is_better": True,
+            "n_gpus": 1, "steps": steps, "warmup": args.warmup, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{count} single-period instances of the batch workload (every {step}th, "
+                                   f"n {min(int(p.F.shape[0]) for p in probs)}-{max(int(p.F.shape[0]) for p in probs)}), "
+                                   f"tol {args.tol}, joint: one CTA per instance; plain: ff_solve_batch, "
+                                   "default schedule"},
+            "joint": {"solved": ok_j, "ms_per_call": mj, "iterations_mean": float(it_j.mean()),
+                      "iterations_median": float(np.median(it_j)),
+                      "mu_rounds_per_iteration": float(np.mean([i["threshold_rounds"] / max(1, i["iterations"])
+                                                                for i in jinfo])),
+                      "instance_seconds_mean": float(np.mean([i["seconds"] for i in jinfo]))},
+            "plain": {"solved": ok_p, "ms_per_call": mp, "iterations_mean": float(it_p.mean()),
+                      "iterations_median": float(np.median(it_p)),
+                      "instance_seconds_mean": float(np.mean([i["seconds"] for i in pinfo]))},
+            "iterations_ratio_median": float(np.median(it_j / np.maximum(it_p, 1))),
+            "max_abs_w_joint_minus_plain": diff, "oracle_check": checks,
+            "gpu_launches": steps * (1 + plain.solver_launches())}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.workload == "risk":
         return run_risk(args)
+    if args.workload == "joint":
+        return run_joint(args)
     if args.workload == "paper_grid":
         return run_paper_grid(args)
     if args.impl == "reference":

@@ -230,8 +230,9 @@ size_t ff_joint_workspace_size(const ff_problem* probs, int count);
  *   prox(v)_i = argmin_w 0.5 (w - v_i)^2 + tau phi_i(w - w0_i) + mu |w|,
  * with the budget multiplier mu found by a safeguarded Newton iteration, so the
  * only multiplier of the iteration is y_A; the steps, the reflected Halpern
- * scheme, the restarts and the relative KKT test (with the trade multiplier
- * recovered from the prox's optimality condition) are those of ff_solve_batch.
+ * scheme, the restarts and the relative KKT test are those of ff_solve_batch;
+ * the KKT test's trade multiplier is the cost's slope phi'(w - w0), or on the
+ * cost's kink (w = w0) the remainder of the prox's optimality condition.
  * FP64 throughout, one CTA per instance; o->precision must be FF_PREC_F64
  * (else FF_ERR_UNSUPPORTED), every instance single-period (T = 0) with k <= 256
  * and m <= 256 (else FF_ERR_UNSUPPORTED).  warm_start, cluster_size, cta_work,

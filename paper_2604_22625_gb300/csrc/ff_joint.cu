@@ -13,8 +13,9 @@
 //     x_bar = prox_{tau g}(x - tau (grad f(x) + A^T y_A)),
 //     y_bar = p - sigma clip(p / sigma, L, U),  p = y_A + sigma A (2 x_bar - x),
 // with the reflected Halpern scheme, the restarts and the relative KKT test of
-// the plain solver (the trade multiplier of the KKT test is recovered from the
-// prox's optimality condition at x_bar).  FP64 throughout; one CTA of 256
+// the plain solver (the trade multiplier of the KKT test is the cost's slope at
+// x_bar - w0, or on the cost's kink the remainder of the prox's optimality
+// condition, clipped to [-c1, c1]).  FP64 throughout; one CTA of 256
 // threads per instance; the instance's arrays are converted to FP64 in the
 // workspace (F transposed, factor-major, so that every matvec reads
 // consecutive assets).
@@ -410,10 +411,16 @@ __global__ void __launch_bounds__(kJT) joint_kernel(const JInst* __restrict__ in
                 const double gr = -I.al[i] + 2.0 * kap * I.Dd[i] * xb + fw;
                 double aty = 0;
                 for (int j = 0; j < m; ++j) aty += I.Am[(size_t)j * n + i] * yAb[j];
+                // off the cost's kink the multiplier is phi'(x_bar - w0) (the one
+                // subgradient there; exact, unlike the residual (v - x_bar) / tau - ...);
+                // on the kink the optimality condition's remainder, clipped to [-c1, c1]
                 double yd;
-                if (xb != 0.0) yd = (I.v[i] - xb) / tau - nu * jsgn(xb);
-                else if (ai != 0.0) yd = I.pd0[i];
-                else yd = fmin(fmax(I.v[i] / tau, -c1), c1);
+                if (xb != ai) {
+                    const double z = xb - ai;
+                    yd = jsgn(z) * (c1 + (c2 > 0 ? c2 * dexp * pow(fabs(z), dexp - 1.0) : 0.0));
+                } else {
+                    yd = fmin(fmax((I.v[i] - ai) / tau - nu * jsgn(ai), -c1), c1);
+                }
                 I.ydb[i] = yd;
                 const double kty = aty + yd;
                 I.qv[i] = xb - (gr + kty);
