@@ -353,13 +353,23 @@ __global__ void __launch_bounds__(kJT) joint_kernel(const JInst* __restrict__ in
                 dS = sv[1];
                 return sv[0];
             };
-            double dS;
-            const double S0 = S_at(0.0, dS);
-            if (S0 > 1.0) {
-                // bracket [lo, hi] with S(lo) > 1 >= S(hi); Newton steps from the
-                // previous iteration's mu, bisection when a step leaves the bracket
-                double lo = 0.0, hi = INFINITY, mt = mu_prev > 0 ? mu_prev : 0.0, St = S0, dSt = dS;
-                if (mt > 0) St = S_at(mt, dSt);
+            // start at the previous iteration's mu; S(0) is evaluated only when
+            // that point lies inside the budget (mu may then be 0)
+            double lo = 0.0, hi = INFINITY, mt = mu_prev, dSt, St;
+            bool search = true;
+            if (mt > 0.0) {
+                St = S_at(mt, dSt);
+                if (St <= 1.0) {
+                    double d0;
+                    if (S_at(0.0, d0) <= 1.0) search = false;
+                }
+            } else {
+                St = S_at(0.0, dSt);
+                if (St <= 1.0) search = false;
+            }
+            if (search) {
+                // bracket [lo, hi] with S(lo) > 1 >= S(hi); Newton steps, bisection
+                // when a step leaves the bracket
                 bool exact = false;
                 for (int r = 0; r < kMuRounds; ++r) {
                     if (fabs(St - 1.0) <= 1e-15) { exact = true; break; }
