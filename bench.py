@@ -807,15 +807,15 @@ def run_risk(args):
                        "precision": "float32 returns; FP32 chunk sums folded into double-float; FP64 solves"},
             "roofline": {"bound": "hbm", "achieved": alg / mean_s / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": alg / mean_s / 1e9 / peak, "traffic": None,
-                         "kernel": "risk_prep_kernel + risk_stream_kernel + risk_finish_kernel (one "
-                                   "ff_risk_estimate call, timed as a whole)",
+                         "kernel": "risk_prep_kernel + risk_ginv_kernel + risk_stream_kernel + "
+                                   "risk_finish_kernel (one ff_risk_estimate call, timed as a whole)",
                          "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"},
             "oracle_check": check,
             "cpu_baseline": {"value": 1.0 / cpu_s, "unit": unit, "cores": cpu_cores(), "kind": "oracle",
                              "sample": "one window (all 5000 stocks) solved by the oracle"},
             "e2e": {"value": count / e2e_s, "unit": unit, "h2d_bytes_per_step": int(Fh.numel() * 4 + Rh.numel() * 4),
                     "d2h_bytes_per_step": int(out_b.numel() * 8 + out_d.numel() * 8)},
-            "gpu_launches": 3 * steps, "clocks": clocks, "step_ms": ms}
+            "gpu_launches": 4 * steps, "clocks": clocks, "step_ms": ms}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0

@@ -418,7 +418,9 @@ int ff_backward_batch(const ff_problem* probs, int count, const void* const* w, 
  *   ws      : device workspace of ff_risk_workspace_size bytes, 256-byte aligned.
  * 1 <= p <= 8, 2 <= T <= 4096, n >= 1, 1 <= count <= 65535, min_obs >= 2;
  * otherwise FF_ERR_INVALID_ARG (0 from ff_risk_workspace_size), before
- * anything is enqueued.  Asynchronous on `stream`. */
+ * anything is enqueued.  Asynchronous on `stream`: four launches (the suffix
+ * Gram tables and Sigma_f of every window, the inverse Gram matrix of every
+ * first day, one pass over R, the per-stock solve and variance). */
 size_t ff_risk_workspace_size(int count, int T, int n, int p);
 int ff_risk_estimate(int count, int T, int n, int p, const float* F, const float* R, int min_obs, double* beta,
                      double* sigma_f, double* D, int32_t* nobs, void* ws, size_t ws_bytes, void* stream);

@@ -13,13 +13,16 @@
 // One pass over R per window.  With first_i the stock's first day, its normal
 // equations need G_i = sum_{k >= first_i} f_k f_k^T and g_i = sum_{k >= first_i} f_k,
 // which depend on first_i only: risk_prep_kernel tabulates these suffix sums
-// once per window in FP64 (products of FP32 inputs are exact in FP64), with
-// Sigma_f.  risk_stream_kernel streams R once: per stock and row segment,
-// b = sum f_k r_k, s1 = sum r_k, s2 = sum r_k^2 are summed in FP32 over chunks
-// of kChunk rows and each chunk sum is added into a double-float accumulator
-// (an error-free two-sum), so the FP32 rounding is bounded by the chunk
-// length; risk_finish_kernel does the p x p solve and the variance in FP64.
-// The pass is bound by the HBM read of R (4 bytes per return).
+// once per window as double-float pairs (exact products of the FP32 inputs,
+// error-free sums in FP32 arithmetic: GB300's FP64 pipe is a small fraction of
+// its FP32 pipe), with Sigma_f in FP64, and risk_ginv_kernel inverts G_j for
+// every first day j in FP64.  risk_stream_kernel streams R once: per stock and
+// row segment, b = sum f_k r_k, s1 = sum r_k, s2 = sum r_k^2 are summed in FP32
+// over chunks of kChunk rows and each chunk sum is added into a double-float
+// accumulator (an error-free two-sum), so the FP32 rounding is bounded by the
+// chunk length; risk_finish_kernel applies the stock's inverse and forms the
+// variance in FP64.  The pass over R is bound by its HBM read (4 bytes per
+// return).
 #include <math.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -37,110 +40,181 @@ constexpr int kMaxT = 4096;
 
 __host__ __device__ inline int tri(int p) { return p * (p + 1) / 2; }
 
-// per window: [T + 1][tri(p)] suffix Gram, [T + 1][p] suffix factor sums (FP64)
+// per window: [T + 1][tri(p)] suffix Gram, [T + 1][p] suffix factor sums
+// (double-float pairs, 8 bytes each)
 __host__ __device__ inline size_t window_doubles(int T, int p) { return (size_t)(T + 1) * (tri(p) + p); }
 
-__global__ void risk_prep_kernel(const float* __restrict__ F, int T, int p, double* __restrict__ sigma_f,
-                                 double* __restrict__ tables, double* __restrict__ ginv0) {
+// (hi, lo) += a b exactly rounded to double-float: the product of two floats is
+// p + e exactly (e from one FMA), added by an error-free two-sum
+__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    const float sm = hi + p;
+    const float bb = sm - hi;
+    lo += ((hi - (sm - bb)) + (p - bb)) + e;
+    hi = sm;
+}
+__device__ __forceinline__ void df_add2(float& hi, float& lo, float bh, float bl) {
+    const float sm = hi + bh;
+    const float bb = sm - hi;
+    lo += ((hi - (sm - bb)) + (bh - bb)) + bl;
+    hi = sm;
+}
+__device__ __forceinline__ void df_norm(float& hi, float& lo) {
+    const float sm = hi + lo;
+    lo = lo - (sm - hi);
+    hi = sm;
+}
+
+constexpr int kPrepSeg = 32;      // row segments of the suffix scan
+constexpr int kCovPart = 16;      // partial sums per factor-covariance entry
+
+// Per window: the suffix tables G_j = sum_{k >= j} f_k f_k^T (upper triangle) and
+// g_j = sum_{k >= j} f_k as double-float pairs (FP32 arithmetic: each product of
+// two FP32 inputs is exact as a pair, the sums are error-free two-sums, about
+// 48 significant bits), and Sigma_f in FP64 from the mean-removed returns.
+__global__ void __launch_bounds__(256) risk_prep_kernel(const float* __restrict__ F, int T, int p,
+                                                        double* __restrict__ sigma_f, float2* __restrict__ tables) {
     extern __shared__ float fsh[];   // [T][p] factor returns of this window
-    constexpr int kSeg = 8;          // row segments of the parallel suffix scan
-    __shared__ double seg_tot[kSeg][kMaxP * (kMaxP + 1) / 2 + kMaxP];
+    __shared__ float2 seg_tot[kPrepSeg][kMaxP * (kMaxP + 1) / 2 + kMaxP];
+    __shared__ unsigned char ea_s[kMaxP * (kMaxP + 1) / 2], eb_s[kMaxP * (kMaxP + 1) / 2];
     __shared__ double mean_s[kMaxP];
-    __shared__ double cov_part[kMaxP * kMaxP][4];
+    __shared__ double cov_part[kMaxP * kMaxP][kCovPart];
     const int d = blockIdx.x;
     const float* fg = F + (size_t)d * T * p;
     for (int e = threadIdx.x; e < T * p; e += blockDim.x) fsh[e] = fg[e];
+    const int np = tri(p), ne = np + p;
+    if (threadIdx.x == 0) {
+        int e = 0;
+        for (int a = 0; a < p; ++a)
+            for (int b = a; b < p; ++b, ++e) { ea_s[e] = (unsigned char)a; eb_s[e] = (unsigned char)b; }
+    }
     __syncthreads();
     const float* f = fsh;
-    double* tab = tables + (size_t)d * window_doubles(T, p);
-    const int np = tri(p), ne = np + p;
-    // suffix sums, entry e < np the Gram entry (a, b) with a <= b, e >= np the sum of
-    // f_a: segment totals, then the segment offsets, then each segment's running sums
-    auto entry = [&](int e, int k) -> double {
-        int a = 0, b = 0;
-        if (e < np) {
-            int r = e;
-            while (r >= p - a) { r -= p - a; ++a; }
-            b = a + r;
-            return (double)f[(size_t)k * p + a] * (double)f[(size_t)k * p + b];
-        }
-        return (double)f[(size_t)k * p + (e - np)];
+    float2* tab = tables + (size_t)d * window_doubles(T, p);
+    // entry e of row k: f_a f_b (e < np) or f_a (e >= np, as the product f_a * 1)
+    auto factors = [&](int e, int k, float& x, float& y) {
+        if (e < np) { x = f[(size_t)k * p + ea_s[e]]; y = f[(size_t)k * p + eb_s[e]]; }
+        else { x = f[(size_t)k * p + (e - np)]; y = 1.0f; }
     };
-    for (int w = threadIdx.x; w < ne * kSeg; w += blockDim.x) {
+    for (int w = threadIdx.x; w < ne * kPrepSeg; w += blockDim.x) {
         const int e = w % ne, sg = w / ne;
-        const int k0 = (int)((long long)T * sg / kSeg), k1 = (int)((long long)T * (sg + 1) / kSeg);
-        double acc = 0.0;
-        for (int k = k0; k < k1; ++k) acc += entry(e, k);
-        seg_tot[sg][e] = acc;
+        const int k0 = (int)((long long)T * sg / kPrepSeg), k1 = (int)((long long)T * (sg + 1) / kPrepSeg);
+        float hi = 0.f, lo = 0.f;
+        for (int k = k0; k < k1; ++k) {
+            float x, y;
+            factors(e, k, x, y);
+            df_add_prod(hi, lo, x, y);
+        }
+        df_norm(hi, lo);
+        seg_tot[sg][e] = make_float2(hi, lo);
     }
     __syncthreads();
-    for (int w = threadIdx.x; w < ne * kSeg; w += blockDim.x) {
+    for (int w = threadIdx.x; w < ne * kPrepSeg; w += blockDim.x) {
         const int e = w % ne, sg = w / ne;
-        const int k0 = (int)((long long)T * sg / kSeg), k1 = (int)((long long)T * (sg + 1) / kSeg);
-        double acc = 0.0;
-        for (int q = kSeg - 1; q > sg; --q) acc += seg_tot[q][e];   // rows after this segment
-        if (sg == kSeg - 1) tab[(size_t)T * ne + e] = 0.0;
+        const int k0 = (int)((long long)T * sg / kPrepSeg), k1 = (int)((long long)T * (sg + 1) / kPrepSeg);
+        float hi = 0.f, lo = 0.f;
+        for (int q = kPrepSeg - 1; q > sg; --q) df_add2(hi, lo, seg_tot[q][e].x, seg_tot[q][e].y);   // later rows
+        if (sg == kPrepSeg - 1) tab[(size_t)T * ne + e] = make_float2(0.f, 0.f);
         for (int k = k1 - 1; k >= k0; --k) {
-            acc += entry(e, k);
-            tab[(size_t)k * ne + e] = acc;
+            float x, y;
+            factors(e, k, x, y);
+            df_add_prod(hi, lo, x, y);
+            df_norm(hi, lo);
+            tab[(size_t)k * ne + e] = make_float2(hi, lo);
         }
     }
-    // factor covariance: mean-removed, divisor T - 1 (4 partial sums per entry)
-    for (int a = threadIdx.x; a < p; a += blockDim.x) {
-        double sm = 0.0;
-        for (int k = 0; k < T; ++k) sm += (double)f[(size_t)k * p + a];
-        mean_s[a] = sm / (double)T;
+    // factor means from the segment totals, then the mean-removed covariance
+    // (divisor T - 1) in FP64 with kCovPart partial sums per entry
+    if (threadIdx.x < p) {
+        float hi = 0.f, lo = 0.f;
+        for (int q = 0; q < kPrepSeg; ++q) df_add2(hi, lo, seg_tot[q][np + threadIdx.x].x, seg_tot[q][np + threadIdx.x].y);
+        mean_s[threadIdx.x] = ((double)hi + (double)lo) / (double)T;
     }
     __syncthreads();
-    for (int w = threadIdx.x; w < p * p * 4; w += blockDim.x) {
+    for (int w = threadIdx.x; w < p * p * kCovPart; w += blockDim.x) {
         const int e = w % (p * p), part = w / (p * p);
         const int a = e / p, b = e % p;
         double sm = 0.0;
-        for (int k = part; k < T; k += 4)
-            sm += ((double)f[(size_t)k * p + a] - mean_s[a]) * ((double)f[(size_t)k * p + b] - mean_s[b]);
+        if (a <= b)
+            for (int k = part; k < T; k += kCovPart)
+                sm += ((double)f[(size_t)k * p + a] - mean_s[a]) * ((double)f[(size_t)k * p + b] - mean_s[b]);
         cov_part[e][part] = sm;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < p * p; e += blockDim.x)
-        sigma_f[(size_t)d * p * p + e] =
-            (((cov_part[e][0] + cov_part[e][1]) + cov_part[e][2]) + cov_part[e][3]) / (double)(T - 1);
-    // inverse of the whole window's Gram matrix (stocks with a return on every day):
-    // Cholesky and p back-substitutions by one thread (p <= 8)
-    if (threadIdx.x == 0) {
-        double Lm[kMaxP][kMaxP];
-        int e = 0;
-        for (int a = 0; a < p; ++a)
-            for (int b = a; b < p; ++b, ++e) { Lm[b][a] = tab[e]; Lm[a][b] = tab[e]; }
-        bool spd = true;
-        for (int a = 0; a < p; ++a) {
-            double sv = Lm[a][a];
-            for (int c = 0; c < a; ++c) sv -= Lm[a][c] * Lm[a][c];
-            if (!(sv > 0.0)) { spd = false; sv = 1.0; }
-            const double l = sqrt(sv);
-            Lm[a][a] = l;
-            for (int r = a + 1; r < p; ++r) {
-                double t = Lm[r][a];
-                for (int c = 0; c < a; ++c) t -= Lm[r][c] * Lm[a][c];
-                Lm[r][a] = t / l;
-            }
-        }
-        double* gi = ginv0 + (size_t)d * (kMaxP * kMaxP + 1);
-        for (int col = 0; col < p; ++col) {
-            double y[kMaxP], x[kMaxP];
-            for (int a = 0; a < p; ++a) {
-                double t = (a == col) ? 1.0 : 0.0;
-                for (int c = 0; c < a; ++c) t -= Lm[a][c] * y[c];
-                y[a] = t / Lm[a][a];
-            }
-            for (int a = p - 1; a >= 0; --a) {
-                double t = y[a];
-                for (int c = a + 1; c < p; ++c) t -= Lm[c][a] * x[c];
-                x[a] = t / Lm[a][a];
-            }
-            for (int a = 0; a < p; ++a) gi[a * p + col] = x[a];
-        }
-        gi[kMaxP * kMaxP] = spd ? 1.0 : 0.0;
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+        const int a = e / p, b = e % p;
+        const int eu = a <= b ? e : b * p + a;   // the upper-triangle entry
+        double sm = 0.0;
+        for (int q = 0; q < kCovPart; ++q) sm += cov_part[eu][q];
+        sigma_f[(size_t)d * p * p + e] = sm / (double)(T - 1);
     }
+}
+
+// Inverse of the Gram matrix G_j of every first day j < T of every window (one
+// thread per (window, j)): FP64 Cholesky and P back-substitutions; the entry
+// after the P x P inverse is 1 when G_j is positive definite, else 0.
+template <int P>
+__global__ void __launch_bounds__(64) risk_ginv_kernel(int T, const float2* __restrict__ tables,
+                                                       double* __restrict__ ginv) {
+    constexpr int NP = P * (P + 1) / 2;
+    const int d = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= T) return;
+    const float2* row = tables + (size_t)d * window_doubles(T, P) + (size_t)j * (NP + P);
+    double Lm[P][P];
+    {
+        int e = 0;
+#pragma unroll
+        for (int a = 0; a < P; ++a)
+#pragma unroll
+            for (int b = a; b < P; ++b, ++e) {
+                const float2 v = row[e];
+                const double g = (double)v.x + (double)v.y;
+                Lm[b][a] = g;
+                Lm[a][b] = g;
+            }
+    }
+    bool spd = true;
+#pragma unroll
+    for (int a = 0; a < P; ++a) {
+        double sv = Lm[a][a];
+#pragma unroll
+        for (int c = 0; c < a; ++c) sv -= Lm[a][c] * Lm[a][c];
+        if (!(sv > 0.0)) { spd = false; sv = 1.0; }
+        const double l = sqrt(sv);
+        const double il = 1.0 / l;
+        Lm[a][a] = l;
+#pragma unroll
+        for (int r = a + 1; r < P; ++r) {
+            double t = Lm[r][a];
+#pragma unroll
+            for (int c = 0; c < a; ++c) t -= Lm[r][c] * Lm[a][c];
+            Lm[r][a] = t * il;
+        }
+    }
+    double* gi = ginv + ((size_t)d * T + j) * (P * P + 1);
+#pragma unroll
+    for (int col = 0; col < P; ++col) {
+        double y[P], x[P];
+#pragma unroll
+        for (int a = 0; a < P; ++a) {
+            double t = (a == col) ? 1.0 : 0.0;
+#pragma unroll
+            for (int c = 0; c < a; ++c) t -= Lm[a][c] * y[c];
+            y[a] = t / Lm[a][a];
+        }
+#pragma unroll
+        for (int a = P - 1; a >= 0; --a) {
+            double t = y[a];
+#pragma unroll
+            for (int c = a + 1; c < P; ++c) t -= Lm[c][a] * x[c];
+            x[a] = t / Lm[a][a];
+        }
+#pragma unroll
+        for (int a = 0; a < P; ++a) gi[a * P + col] = x[a];
+    }
+    gi[P * P] = spd ? 1.0 : 0.0;
 }
 
 // error-free fold of an FP32 chunk sum x into the pair (hi, lo)
@@ -253,11 +327,12 @@ __device__ __forceinline__ void finish_moments(const double (&x)[P], const doubl
     *Dout = (sq - st * st / (double)cnt) / (double)(cnt - 1);
 }
 
-// One thread per stock: history rule, normal equations over the stock's days
-// (suffix Gram table, FP64 Cholesky), residual variance from the moments.
+// One thread per stock: history rule, then beta = G_first^{-1} b from the
+// window's precomputed inverse for the stock's first day, and the residual
+// variance from the moments.
 template <int P>
-__global__ void risk_finish_kernel(int T, int n, int min_obs, const double* __restrict__ tables,
-                                   const double* __restrict__ ginv0, const double* __restrict__ sums,
+__global__ void risk_finish_kernel(int T, int n, int min_obs, const float2* __restrict__ tables,
+                                   const double* __restrict__ ginv, const double* __restrict__ sums,
                                    const int* __restrict__ hist, double* __restrict__ beta, double* __restrict__ D,
                                    int32_t* __restrict__ nobs) {
     constexpr int NS = P + 2;
@@ -271,80 +346,40 @@ __global__ void risk_finish_kernel(int T, int n, int min_obs, const double* __re
     const int cnt = any ? T - first : 0;
     double* bo = beta + si * P;
     if (nobs) nobs[si] = regular ? cnt : -1;
-    if (!regular || cnt < min_obs || cnt < 2) {
+    const double* gi = ginv + ((size_t)d * T + (any ? first : 0)) * (P * P + 1);
+    if (!regular || cnt < min_obs || cnt < 2 || gi[P * P] == 0.0) {
 #pragma unroll
         for (int j = 0; j < P; ++j) bo[j] = 0.0;
         D[si] = NAN;
+        if (nobs && regular && cnt >= min_obs && cnt >= 2) nobs[si] = -2;   // singular Gram matrix
         return;
     }
     constexpr int NP = P * (P + 1) / 2;
-    const double* tab = tables + (size_t)d * window_doubles(T, P) + (size_t)first * (NP + P);
+    const float2* tab = tables + (size_t)d * window_doubles(T, P) + (size_t)first * (NP + P);
     double b[P], g1[P], x[P];
 #pragma unroll
     for (int j = 0; j < P; ++j) {
         b[j] = sums[si * NS + j];
-        g1[j] = tab[NP + j];
+        const float2 v = tab[NP + j];
+        g1[j] = (double)v.x + (double)v.y;
     }
-    const double* gi = ginv0 + (size_t)d * (kMaxP * kMaxP + 1);
-    if (first == 0 && gi[kMaxP * kMaxP] != 0.0) {
-        // a return on every day: the window's Gram inverse, computed once per window
-#pragma unroll
-        for (int a = 0; a < P; ++a) {
-            double t = 0.0;
-#pragma unroll
-            for (int c2 = 0; c2 < P; ++c2) t += gi[a * P + c2] * b[c2];
-            x[a] = t;
-        }
-        finish_moments<P>(x, b, g1, sums + si * NS, cnt, beta + si * P, D + si);
-        return;
-    }
-    double Lm[P][P];
-    {
-        int e = 0;
-        for (int a = 0; a < P; ++a)
-            for (int bb = a; bb < P; ++bb, ++e) { Lm[bb][a] = tab[e]; Lm[a][bb] = tab[e]; }
-    }
-    bool spd = true;
 #pragma unroll
     for (int a = 0; a < P; ++a) {
-        double s = Lm[a][a];
-        for (int c = 0; c < a; ++c) s -= Lm[a][c] * Lm[a][c];
-        if (!(s > 0.0)) { spd = false; s = 1.0; }
-        const double l = sqrt(s);
-        Lm[a][a] = l;
-        for (int r = a + 1; r < P; ++r) {
-            double t = Lm[r][a];
-            for (int c = 0; c < a; ++c) t -= Lm[r][c] * Lm[a][c];
-            Lm[r][a] = t / l;
-        }
-    }
-    double y[P];
+        double t = 0.0;
 #pragma unroll
-    for (int a = 0; a < P; ++a) {
-        double t = b[a];
-        for (int c = 0; c < a; ++c) t -= Lm[a][c] * y[c];
-        y[a] = t / Lm[a][a];
-    }
-#pragma unroll
-    for (int a = P - 1; a >= 0; --a) {
-        double t = y[a];
-        for (int c = a + 1; c < P; ++c) t -= Lm[c][a] * x[c];
-        x[a] = t / Lm[a][a];
-    }
-    if (!spd) {
-#pragma unroll
-        for (int j = 0; j < P; ++j) bo[j] = 0.0;
-        D[si] = NAN;
-        if (nobs) nobs[si] = -2;
-        return;
+        for (int c2 = 0; c2 < P; ++c2) t += gi[a * P + c2] * b[c2];
+        x[a] = t;
     }
     finish_moments<P>(x, b, g1, sums + si * NS, cnt, bo, D + si);
 }
 
 template <int P>
 cudaError_t launch_stream(const float* F, const float* R, int count, int T, int n, int min_obs,
-                          const double* tables, const double* ginv0, double* sums, int* hist, double* beta,
+                          const float2* tables, double* ginv, double* sums, int* hist, double* beta,
                           double* D, int32_t* nobs, cudaStream_t stream) {
+    risk_ginv_kernel<P><<<dim3((unsigned)((T + 63) / 64), (unsigned)count), 64, 0, stream>>>(T, tables, ginv);
+    cudaError_t e0 = cudaGetLastError();
+    if (e0 != cudaSuccess) return e0;
     const size_t smem = (size_t)T * P * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(risk_stream_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
@@ -354,7 +389,7 @@ cudaError_t launch_stream(const float* F, const float* R, int count, int T, int 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 grid2((unsigned)((n + 127) / 128), (unsigned)count);
-    risk_finish_kernel<P><<<grid2, 128, 0, stream>>>(T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs);
+    risk_finish_kernel<P><<<grid2, 128, 0, stream>>>(T, n, min_obs, tables, ginv, sums, hist, beta, D, nobs);
     return cudaGetLastError();
 }
 
@@ -372,8 +407,9 @@ int risk_fail(cudaError_t e, const char* where) {
 extern "C" {
 
 static size_t risk_tables_bytes(int count, int T, int p) {
-    // suffix tables, then the inverse Gram matrix of every window (kMaxP^2 + 1 doubles)
-    return ((size_t)count * (ff::window_doubles(T, p) + ff::kMaxP * ff::kMaxP + 1) * sizeof(double) + 255) / 256 * 256;
+    // suffix tables (double-float pairs), then the inverse Gram matrix of every
+    // first day of every window (p^2 + 1 doubles each)
+    return ((size_t)count * (ff::window_doubles(T, p) + (size_t)T * (p * p + 1)) * sizeof(double) + 255) / 256 * 256;
 }
 
 size_t ff_risk_workspace_size(int count, int T, int n, int p) {
@@ -390,25 +426,25 @@ int ff_risk_estimate(int count, int T, int n, int p, const float* F, const float
     if (!ws || ((uintptr_t)ws % 256) != 0 || ws_bytes < need) return FF_ERR_WORKSPACE;
     if ((long long)(n + ff::kRiskThreads - 1) / ff::kRiskThreads > 2147483647LL) return FF_ERR_UNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
-    double* tables = (double*)ws;
-    double* ginv0 = tables + (size_t)count * ff::window_doubles(T, p);
+    float2* tables = (float2*)ws;
+    double* ginv = (double*)(tables + (size_t)count * ff::window_doubles(T, p));
     double* sums = (double*)((unsigned char*)ws + risk_tables_bytes(count, T, p));
     int* hist = (int*)((unsigned char*)sums + ((size_t)count * n * (p + 2) * sizeof(double) + 255) / 256 * 256);
     const size_t fsmem = (size_t)T * p * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(ff::risk_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
     if (e != cudaSuccess) return ff::risk_fail(e, "risk_prep_kernel attribute");
-    ff::risk_prep_kernel<<<count, 256, fsmem, st>>>(F, T, p, sigma_f, tables, ginv0);
+    ff::risk_prep_kernel<<<count, 256, fsmem, st>>>(F, T, p, sigma_f, tables);
     e = cudaGetLastError();
     if (e != cudaSuccess) return ff::risk_fail(e, "risk_prep_kernel launch");
     switch (p) {
-        case 1: e = ff::launch_stream<1>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
-        case 2: e = ff::launch_stream<2>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
-        case 3: e = ff::launch_stream<3>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
-        case 4: e = ff::launch_stream<4>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
-        case 5: e = ff::launch_stream<5>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
-        case 6: e = ff::launch_stream<6>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
-        case 7: e = ff::launch_stream<7>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
-        default: e = ff::launch_stream<8>(F, R, count, T, n, min_obs, tables, ginv0, sums, hist, beta, D, nobs, st); break;
+        case 1: e = ff::launch_stream<1>(F, R, count, T, n, min_obs, tables, ginv, sums, hist, beta, D, nobs, st); break;
+        case 2: e = ff::launch_stream<2>(F, R, count, T, n, min_obs, tables, ginv, sums, hist, beta, D, nobs, st); break;
+        case 3: e = ff::launch_stream<3>(F, R, count, T, n, min_obs, tables, ginv, sums, hist, beta, D, nobs, st); break;
+        case 4: e = ff::launch_stream<4>(F, R, count, T, n, min_obs, tables, ginv, sums, hist, beta, D, nobs, st); break;
+        case 5: e = ff::launch_stream<5>(F, R, count, T, n, min_obs, tables, ginv, sums, hist, beta, D, nobs, st); break;
+        case 6: e = ff::launch_stream<6>(F, R, count, T, n, min_obs, tables, ginv, sums, hist, beta, D, nobs, st); break;
+        case 7: e = ff::launch_stream<7>(F, R, count, T, n, min_obs, tables, ginv, sums, hist, beta, D, nobs, st); break;
+        default: e = ff::launch_stream<8>(F, R, count, T, n, min_obs, tables, ginv, sums, hist, beta, D, nobs, st); break;
     }
     if (e != cudaSuccess) return ff::risk_fail(e, "risk_stream_kernel launch");
     return FF_OK;
