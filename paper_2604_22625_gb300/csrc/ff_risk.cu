@@ -33,7 +33,7 @@ namespace ff {
 namespace {
 
 constexpr int kRiskThreads = 256;
-constexpr int kChunk = 8;          // rows summed in FP32 before a double-float fold
+constexpr int kChunk = 16;         // rows summed in FP32 before a double-float fold
 constexpr int kUnroll = 16;        // returns loaded ahead per thread
 constexpr int kMaxP = 8;
 constexpr int kMaxT = 4096;
@@ -74,8 +74,10 @@ constexpr int kCovPart = 16;      // partial sums per factor-covariance entry
 // two FP32 inputs is exact as a pair, the sums are error-free two-sums, about
 // 48 significant bits), and Sigma_f in FP64 from the mean-removed returns.
 __global__ void __launch_bounds__(256) risk_prep_kernel(const float* __restrict__ F, int T, int p,
-                                                        double* __restrict__ sigma_f, float2* __restrict__ tables) {
-    extern __shared__ float fsh[];   // [T][p] factor returns of this window
+                                                        double* __restrict__ sigma_f, float2* __restrict__ tables,
+                                                        int cen_smem) {
+    extern __shared__ float fsh[];   // [T][p] factor returns of this window; then, with cen_smem,
+                                     // [T][p] centred returns in FP64
     __shared__ float2 seg_tot[kPrepSeg][kMaxP * (kMaxP + 1) / 2 + kMaxP];
     __shared__ unsigned char ea_s[kMaxP * (kMaxP + 1) / 2], eb_s[kMaxP * (kMaxP + 1) / 2];
     __shared__ double mean_s[kMaxP];
@@ -125,21 +127,29 @@ __global__ void __launch_bounds__(256) risk_prep_kernel(const float* __restrict_
         }
     }
     // factor means from the segment totals, then the mean-removed covariance
-    // (divisor T - 1) in FP64 with kCovPart partial sums per entry
+    // (divisor T - 1) in FP64 with kCovPart partial sums per entry; the centred
+    // returns are formed once in shared memory when they fit (cen_smem)
     if (threadIdx.x < p) {
         float hi = 0.f, lo = 0.f;
         for (int q = 0; q < kPrepSeg; ++q) df_add2(hi, lo, seg_tot[q][np + threadIdx.x].x, seg_tot[q][np + threadIdx.x].y);
         mean_s[threadIdx.x] = ((double)hi + (double)lo) / (double)T;
     }
     __syncthreads();
-    for (int w = threadIdx.x; w < p * p * kCovPart; w += blockDim.x) {
-        const int e = w % (p * p), part = w / (p * p);
-        const int a = e / p, b = e % p;
+    double* cen = (double*)(fsh + ((size_t)T * p + 1) / 2 * 2);   // [T][p], 8-byte aligned after the floats
+    if (cen_smem) {
+        for (int e = threadIdx.x; e < T * p; e += blockDim.x) cen[e] = (double)f[e] - mean_s[e % p];
+        __syncthreads();
+    }
+    for (int w = threadIdx.x; w < np * kCovPart; w += blockDim.x) {
+        const int e = w % np, part = w / np;
+        const int a = ea_s[e], b = eb_s[e];
         double sm = 0.0;
-        if (a <= b)
+        if (cen_smem)
+            for (int k = part; k < T; k += kCovPart) sm += cen[(size_t)k * p + a] * cen[(size_t)k * p + b];
+        else
             for (int k = part; k < T; k += kCovPart)
                 sm += ((double)f[(size_t)k * p + a] - mean_s[a]) * ((double)f[(size_t)k * p + b] - mean_s[b]);
-        cov_part[e][part] = sm;
+        cov_part[a * p + b][part] = sm;
     }
     __syncthreads();
     for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
@@ -176,6 +186,7 @@ __global__ void __launch_bounds__(64) risk_ginv_kernel(int T, const float2* __re
             }
     }
     bool spd = true;
+    double il[P];   // reciprocals of the factor's diagonal: one division per pivot
 #pragma unroll
     for (int a = 0; a < P; ++a) {
         double sv = Lm[a][a];
@@ -183,14 +194,14 @@ __global__ void __launch_bounds__(64) risk_ginv_kernel(int T, const float2* __re
         for (int c = 0; c < a; ++c) sv -= Lm[a][c] * Lm[a][c];
         if (!(sv > 0.0)) { spd = false; sv = 1.0; }
         const double l = sqrt(sv);
-        const double il = 1.0 / l;
+        il[a] = 1.0 / l;
         Lm[a][a] = l;
 #pragma unroll
         for (int r = a + 1; r < P; ++r) {
             double t = Lm[r][a];
 #pragma unroll
             for (int c = 0; c < a; ++c) t -= Lm[r][c] * Lm[a][c];
-            Lm[r][a] = t * il;
+            Lm[r][a] = t * il[a];
         }
     }
     double* gi = ginv + ((size_t)d * T + j) * (P * P + 1);
@@ -202,14 +213,14 @@ __global__ void __launch_bounds__(64) risk_ginv_kernel(int T, const float2* __re
             double t = (a == col) ? 1.0 : 0.0;
 #pragma unroll
             for (int c = 0; c < a; ++c) t -= Lm[a][c] * y[c];
-            y[a] = t / Lm[a][a];
+            y[a] = t * il[a];
         }
 #pragma unroll
         for (int a = P - 1; a >= 0; --a) {
             double t = y[a];
 #pragma unroll
             for (int c = a + 1; c < P; ++c) t -= Lm[c][a] * x[c];
-            x[a] = t / Lm[a][a];
+            x[a] = t * il[a];
         }
 #pragma unroll
         for (int a = 0; a < P; ++a) gi[a * P + col] = x[a];
@@ -225,18 +236,20 @@ __device__ __forceinline__ void fold(float& hi, float& lo, float x) {
     hi = s;
 }
 
-// Streaming pass.  A block holds kStocks consecutive stocks (one warp's width,
-// so every row read is one 128-byte line per warp) and kSegs row segments: warp
-// w sums rows [w T / kSegs, (w + 1) T / kSegs) of the block's stocks, so that
-// many independent loads are in flight per SM.  Per stock and segment: the
-// double-float sums of f_k r_k (P), r_k, r_k^2, the first row with a return and
-// the last row without one; the segments are combined in shared memory (pairs
-// added in segment order) and written to the workspace for risk_finish_kernel.
-constexpr int kStocks = 32;
+// Streaming pass.  A thread holds two adjacent stocks (one 8-byte load per row
+// when n is even, so a warp reads 256 consecutive bytes of a row) and a block
+// kSegs row segments of kStocks = 64 stocks: warp w sums rows
+// [w T / kSegs, (w + 1) T / kSegs), so that many independent loads are in
+// flight per SM.  Per stock and segment: the double-float sums of f_k r_k (P),
+// r_k, r_k^2, the first row with a return and the last row without one; the
+// segments are combined in shared memory (pairs added in segment order) and
+// written to the workspace for risk_finish_kernel.
+constexpr int kLanes = 32;
+constexpr int kStocks = 2 * kLanes;
 constexpr int kSegs = 8;
 
-template <int P>
-__global__ void __launch_bounds__(kStocks * kSegs)
+template <int P, bool kVec>
+__global__ void __launch_bounds__(kLanes * kSegs)
 risk_stream_kernel(const float* __restrict__ F, const float* __restrict__ R, int T, int n,
                    double* __restrict__ sums, int* __restrict__ hist) {
     extern __shared__ float f_s[];   // [T][P] factor returns of this window
@@ -247,47 +260,77 @@ risk_stream_kernel(const float* __restrict__ F, const float* __restrict__ R, int
     const float* fw = F + (size_t)d * T * P;
     for (int e = threadIdx.x; e < T * P; e += blockDim.x) f_s[e] = fw[e];
     __syncthreads();
-    const int lane = threadIdx.x % kStocks, seg = threadIdx.x / kStocks;
-    const int i = blockIdx.x * kStocks + lane;
+    const int lane = threadIdx.x % kLanes, seg = threadIdx.x / kLanes;
+    const int i0 = blockIdx.x * kStocks + 2 * lane;
     const int k_lo = (int)((long long)T * seg / kSegs), k_hi = (int)((long long)T * (seg + 1) / kSegs);
-    float hi[NS], lo[NS], ch[NS];
+    float hi[2][NS], lo[2][NS], ch[2][NS];
 #pragma unroll
-    for (int j = 0; j < NS; ++j) { hi[j] = 0.f; lo[j] = 0.f; ch[j] = 0.f; }
-    int first = 1 << 30, lastnan = -1, inchunk = 0;
-    if (i < n) {
-        const float* col = R + (size_t)d * T * n + i;
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int j = 0; j < NS; ++j) { hi[q][j] = 0.f; lo[q][j] = 0.f; ch[q][j] = 0.f; }
+    int first[2] = {1 << 30, 1 << 30}, lastnan[2] = {-1, -1}, inchunk = 0;
+    if (i0 < n) {
+        const bool two = i0 + 1 < n;
+        const float* col = R + (size_t)d * T * n + i0;
         for (int k0 = k_lo; k0 < k_hi; k0 += kUnroll) {
-            float rv[kUnroll];
+            float2 rv[kUnroll];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) rv[u] = (k0 + u < k_hi) ? __ldg(col + (size_t)(k0 + u) * n) : NAN;
+            for (int u = 0; u < kUnroll; ++u) {
+                const int k = k0 + u;
+                if (k < k_hi) {
+                    const float* pk = col + (size_t)k * n;
+                    if constexpr (kVec) rv[u] = two ? __ldg((const float2*)pk) : make_float2(__ldg(pk), NAN);
+                    else rv[u] = make_float2(__ldg(pk), two ? __ldg(pk + 1) : NAN);
+                } else {
+                    rv[u] = make_float2(NAN, NAN);
+                }
+            }
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
                 const int k = k0 + u;
                 if (k >= k_hi) break;
-                const float r = rv[u];
-                if (isnan(r)) { lastnan = k; continue; }
-                first = min(first, k);
                 const float* fk = f_s + k * P;
+                float fv[P];
 #pragma unroll
-                for (int j = 0; j < P; ++j) ch[j] = fmaf(fk[j], r, ch[j]);
-                ch[P] += r;
-                ch[P + 1] = fmaf(r, r, ch[P + 1]);
+                for (int j = 0; j < P; ++j) fv[j] = fk[j];
+                const float r2[2] = {rv[u].x, rv[u].y};
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const float r = r2[q];
+                    if (isnan(r)) { lastnan[q] = k; continue; }
+                    first[q] = min(first[q], k);
+#pragma unroll
+                    for (int j = 0; j < P; ++j) ch[q][j] = fmaf(fv[j], r, ch[q][j]);
+                    ch[q][P] += r;
+                    ch[q][P + 1] = fmaf(r, r, ch[q][P + 1]);
+                }
+                // fold every kChunk rows (NaN rows count: a chunk holds at most kChunk terms)
                 if (++inchunk == kChunk) {
 #pragma unroll
-                    for (int j = 0; j < NS; ++j) { fold(hi[j], lo[j], ch[j]); ch[j] = 0.f; }
+                    for (int q = 0; q < 2; ++q)
+#pragma unroll
+                        for (int j = 0; j < NS; ++j) { fold(hi[q][j], lo[q][j], ch[q][j]); ch[q][j] = 0.f; }
                     inchunk = 0;
                 }
             }
         }
 #pragma unroll
-        for (int j = 0; j < NS; ++j) fold(hi[j], lo[j], ch[j]);
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int j = 0; j < NS; ++j) fold(hi[q][j], lo[q][j], ch[q][j]);
     }
 #pragma unroll
-    for (int j = 0; j < NS; ++j) { red_hi[seg][j][lane] = hi[j]; red_lo[seg][j][lane] = lo[j]; }
-    red_first[seg][lane] = first;
-    red_lastnan[seg][lane] = lastnan;
+    for (int q = 0; q < 2; ++q) {
+#pragma unroll
+        for (int j = 0; j < NS; ++j) {
+            red_hi[seg][j][2 * lane + q] = hi[q][j];
+            red_lo[seg][j][2 * lane + q] = lo[q][j];
+        }
+        red_first[seg][2 * lane + q] = first[q];
+        red_lastnan[seg][2 * lane + q] = lastnan[q];
+    }
     __syncthreads();
-    // combine the segments (fixed order) and write: threads (j, lane), j < NS
+    // combine the segments (fixed order) and write: threads (j, stock), j < NS
     for (int e = threadIdx.x; e < NS * kStocks; e += blockDim.x) {
         const int j = e / kStocks, l = e % kStocks;
         const int ii = blockIdx.x * kStocks + l;
@@ -381,11 +424,13 @@ cudaError_t launch_stream(const float* F, const float* R, int count, int T, int 
     cudaError_t e0 = cudaGetLastError();
     if (e0 != cudaSuccess) return e0;
     const size_t smem = (size_t)T * P * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(risk_stream_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    // 8-byte row loads when every row of a thread's stock pair starts 8-byte aligned
+    const bool vec = (n % 2 == 0) && ((uintptr_t)R % 8 == 0);
+    auto kern = vec ? risk_stream_kernel<P, true> : risk_stream_kernel<P, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((n + kStocks - 1) / kStocks), (unsigned)count);
-    risk_stream_kernel<P><<<grid, kStocks * kSegs, smem, stream>>>(F, R, T, n, sums, hist);
+    kern<<<grid, kLanes * kSegs, smem, stream>>>(F, R, T, n, sums, hist);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 grid2((unsigned)((n + 127) / 128), (unsigned)count);
@@ -431,9 +476,13 @@ int ff_risk_estimate(int count, int T, int n, int p, const float* F, const float
     double* sums = (double*)((unsigned char*)ws + risk_tables_bytes(count, T, p));
     int* hist = (int*)((unsigned char*)sums + ((size_t)count * n * (p + 2) * sizeof(double) + 255) / 256 * 256);
     const size_t fsmem = (size_t)T * p * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(ff::risk_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
+    // the centred returns in FP64 join the floats in shared memory when both fit in 160 KB
+    const size_t csmem = ((size_t)T * p + 1) / 2 * 2 * sizeof(float) + (size_t)T * p * sizeof(double);
+    const int cen_smem = csmem <= 160u * 1024u ? 1 : 0;
+    const size_t psmem = cen_smem ? csmem : fsmem;
+    cudaError_t e = cudaFuncSetAttribute(ff::risk_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
     if (e != cudaSuccess) return ff::risk_fail(e, "risk_prep_kernel attribute");
-    ff::risk_prep_kernel<<<count, 256, fsmem, st>>>(F, T, p, sigma_f, tables);
+    ff::risk_prep_kernel<<<count, 256, psmem, st>>>(F, T, p, sigma_f, tables, cen_smem);
     e = cudaGetLastError();
     if (e != cudaSuccess) return ff::risk_fail(e, "risk_prep_kernel launch");
     switch (p) {

@@ -2,11 +2,12 @@
 oracle (oracle/risk.py) on the same float32 returns, element by element.
 
 Tolerances from the arithmetic: the factor covariance and the Gram matrices
-are FP64 sums of exact products of FP32 inputs (1e-12 relative); b = F^T r,
-sum r and sum r^2 are FP32 sums over chunks of 8 days folded into
-double-float accumulators, so each carries at most 8 u32 = 4.8e-7 of the sum
-of its terms' magnitudes: beta to 1e-5 absolute (loadings are O(1)) and D to
-1e-5 relative.  History counts and the estimated / not-estimated decision are
+are sums of exact products of FP32 inputs (FP64 for Sigma_f, 1e-12 relative;
+double-float pairs of about 48 bits for the Gram tables); b = F^T r, sum r
+and sum r^2 are FP32 sums over chunks of 16 days folded into double-float
+accumulators, so each carries at most 16 u32 = 9.5e-7 of the sum of its
+terms' magnitudes: beta to 1e-5 absolute (loadings are O(1)) and D to 1e-5
+relative.  History counts and the estimated / not-estimated decision are
 exact."""
 import numpy as np
 import pytest
