@@ -271,8 +271,7 @@ int ff_solve_joint_batch(const ff_problem* probs, int count, const ff_options* o
  *   are rejected with FF_ERR_WORKSPACE before anything is enqueued;
  *   ff_last_error() then states the bytes needed.
  * - The first call on each device looks up the array's device address with
- *   cudaGetSymbolAddress (with that device current) and caches it; make that
- *   first call before any stream capture.
+ *   cudaGetSymbolAddress (with that device current) and caches it.
  * - Every call on a device shares the one array, and it keeps the previous
  *   call's contents (nothing in it needs to start at zero: each solve writes
  *   every region before reading it).  Calls that overlap on the GPU (other

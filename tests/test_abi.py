@@ -196,3 +196,25 @@ def test_package_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import oracle|from oracle)", src, re.M), f
+
+
+def test_joint_host_checks(lib):
+    """Workspace size and argument checks of the joint prox variant (host only):
+    about 8 n (k + m + 12) bytes per instance; FP64 only; single-period only;
+    k, m <= 256; a short workspace is refused before anything is enqueued."""
+    single = _placeholder_problem(n=1000, k=10, m=10)
+    one = (_lib.ff_problem * 1)(single)
+    ws1 = _lib.ff_joint_workspace_size(one, 1)
+    est = 8 * 1000 * (10 + 10 + 12)
+    assert est <= ws1 <= est + 16 * 256 + 4096
+    multi = (_lib.ff_problem * 1)(_placeholder_problem(T=5))
+    assert _lib.ff_joint_workspace_size(multi, 1) == 0
+    o32 = _lib.default_options(precision=_lib.FF_PREC_F32)
+    o64 = _lib.default_options(precision=_lib.FF_PREC_F64)
+    assert _lib.ff_solve_joint_batch(one, 1, o32, 4096, ws1, 4096, [4096]) == _lib.FF_ERR_UNSUPPORTED
+    assert _lib.ff_solve_joint_batch(multi, 1, o64, 4096, ws1, 4096, [4096]) == _lib.FF_ERR_UNSUPPORTED
+    wide = (_lib.ff_problem * 1)(_placeholder_problem(n=1000, k=300, m=10))
+    assert _lib.ff_solve_joint_batch(wide, 1, o64, 4096, 1 << 30, 4096, [4096]) == _lib.FF_ERR_UNSUPPORTED
+    assert _lib.ff_solve_joint_batch(one, 1, o64, 4096, ws1 - 256, 4096, [4096]) == _lib.FF_ERR_WORKSPACE
+    assert _lib.ff_solve_joint_batch(one, 1, o64, 4096 + 8, ws1, 4096, [4096]) == _lib.FF_ERR_WORKSPACE
+    assert _lib.ff_solve_joint_batch(one, 1, o64, 4096, ws1, 4096, [None]) == _lib.FF_ERR_INVALID_ARG
