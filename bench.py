@@ -55,11 +55,17 @@ def parse_args(argv=None):
     ap.add_argument("--grid-n", type=int, default=2000, help="paper_grid: assets per instance")
     ap.add_argument("--joint-count", type=int, default=64, help="joint: single-period instances compared")
     ap.add_argument("--grid-dates", type=int, default=21, help="paper_grid: instances (dates) per setting")
+    ap.add_argument("--grid-kinds", default="single,multi", help="paper_grid: comma-separated kinds to run")
     ap.add_argument("--eta", default="literal", choices=["literal", "inverted"], help="paper_grid: reading "
                     "of the intraday cost profile")
     ap.add_argument("--primal-weight", type=int, default=-1, help="1/0: adaptive primal weight on/off "
                     "(-1: the library default)")
     ap.add_argument("--max-iter", type=int, default=0, help="iteration cap (profiling runs only)")
+    ap.add_argument("--cta-work", type=float, default=16384.0,
+                    help="batch workload: asset-periods per CTA (the fastest point of the autotuner's grid "
+                         "on this batch in a sweep on GB300; 0 = the library default)")
+    ap.add_argument("--check-every", type=int, default=128,
+                    help="batch workload: iterations between KKT checks (as --cta-work; 0 = library default)")
     ap.add_argument("--tuned", action="store_true", help="take cta_work / check_every from the autotuner "
                     "(paper_2604_22625_gb300.tune; times candidates on a sample once, then cached)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -433,10 +439,20 @@ def run_ours(args):
     if diff:
         opt_kw["tol"] = 1e-7
     tuned = None
+    schedule = "library default (cta_work 8192, check_every 64)"
     if args.tuned:
         from paper_2604_22625_gb300 import tune
         tuned = tune.tune(probs, precision=precision, tol=opt_kw["tol"], device=torch.cuda.get_device_name(dev))
         opt_kw.update(tuned.options())
+        schedule = f"autotuned now: {tuned.options()}"
+    elif args.workload == "batch" and (args.cta_work > 0 or args.check_every > 0):
+        if args.cta_work > 0:
+            opt_kw["cta_work"] = args.cta_work
+        if args.check_every > 0:
+            opt_kw["check_every"] = args.check_every
+        schedule = (f"cta_work {opt_kw.get('cta_work', 8192.0):g}, check_every {opt_kw.get('check_every', 64)}: "
+                    "the fastest point of the autotuner's grid (cta_work 4096/8192/16384, check_every 32/64/128) "
+                    "for this batch in a sweep on GB300")
     # duals are kept so that the oracle can evaluate the relative KKT of the timed outputs
     runner = api.BatchRunner(probs, precision=precision, device=str(dev), duals=True, **opt_kw)
     tol_ok = opt_kw["tol"]
@@ -646,7 +662,7 @@ def run_ours(args):
                              f"{runner.ws_bytes / 2**20:.0f} MiB workspace vs {l2_mb:.0f} MiB L2)",
                        "parallelism": f"replicas x{ws} (one batch per GPU)" if ws > 1 else "1 GPU",
                        "max_iter_cap": args.max_iter or None,
-                       "schedule": tuned.options() if tuned is not None else "default (cta_work 8192, check_every 64)",
+                       "schedule": schedule,
                        "graph": use_graph},
             "solved": solved, "max_rel_kkt": kkt_max,
             "escalated_fp64": max(escalated_steps, default=0),
@@ -851,7 +867,8 @@ def run_paper_grid(args):
     rows, pend = [], []
     grid_kw = {} if args.primal_weight < 0 else {"primal_weight": args.primal_weight}
     t_all = time.perf_counter()
-    for kind in ("single", "multi"):
+    kinds = [k for k in ("single", "multi") if k in args.grid_kinds.split(",")]
+    for kind in kinds:
         for lam23 in S.PAPER_LAMBDA23:
             for lam1 in S.PAPER_LAMBDA1:
                 times, its, solved, esc = [], [], 0, 0
@@ -880,9 +897,10 @@ def run_paper_grid(args):
     pool.close()
     pool.join()
     line = {"metric": "paper lambda grid: solved count and SGM1 (s) per setting", "unit": "s",
-            "config": {"workload": f"synthetic paper-shaped instances: n={args.grid_n}, p=6 factors with a full "
-                                   f"factor covariance, T=10 (multi, eta {args.eta}), {args.grid_dates} per "
-                                   f"setting, FP32, tol {args.tol}, 360 s limit, one solve call each"},
+            "config": {"workload": f"synthetic paper-shaped instances ({'+'.join(kinds)}): n={args.grid_n}, p=6 "
+                                   f"factors with a full factor covariance, T=10 (multi, eta {args.eta}), "
+                                   f"{args.grid_dates} per setting, FP32, tol {args.tol}, 360 s limit, one solve "
+                                   "call each"},
             "wall_s": wall, "rows": rows}
     print(json.dumps(line), flush=True)
     return 0
