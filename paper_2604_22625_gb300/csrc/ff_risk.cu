@@ -34,7 +34,7 @@ namespace {
 
 constexpr int kRiskThreads = 256;
 constexpr int kChunk = 16;         // rows summed in FP32 before a double-float fold
-constexpr int kUnroll = 16;        // returns loaded ahead per thread
+constexpr int kBatch = 8;          // rows per register buffer of the streaming pass (two buffers)
 constexpr int kMaxP = 8;
 constexpr int kMaxT = 4096;
 
@@ -272,10 +272,10 @@ risk_stream_kernel(const float* __restrict__ F, const float* __restrict__ R, int
     if (i0 < n) {
         const bool two = i0 + 1 < n;
         const float* col = R + (size_t)d * T * n + i0;
-        for (int k0 = k_lo; k0 < k_hi; k0 += kUnroll) {
-            float2 rv[kUnroll];
+        // rows k0 .. k0 + kBatch - 1 of the stock pair (NaN past the segment)
+        auto load = [&](float2 (&rv)[kBatch], int k0) {
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
+            for (int u = 0; u < kBatch; ++u) {
                 const int k = k0 + u;
                 if (k < k_hi) {
                     const float* pk = col + (size_t)k * n;
@@ -285,8 +285,10 @@ risk_stream_kernel(const float* __restrict__ F, const float* __restrict__ R, int
                     rv[u] = make_float2(NAN, NAN);
                 }
             }
+        };
+        auto compute = [&](const float2 (&rv)[kBatch], int k0) {
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
+            for (int u = 0; u < kBatch; ++u) {
                 const int k = k0 + u;
                 if (k >= k_hi) break;
                 const float* fk = f_s + k * P;
@@ -313,6 +315,16 @@ risk_stream_kernel(const float* __restrict__ F, const float* __restrict__ R, int
                     inchunk = 0;
                 }
             }
+        };
+        // two register buffers: the loads of the next batch are in flight while
+        // the current one is summed
+        float2 ra[kBatch], rb[kBatch];
+        load(ra, k_lo);
+        for (int k0 = k_lo; k0 < k_hi; k0 += 2 * kBatch) {
+            load(rb, k0 + kBatch);
+            compute(ra, k0);
+            load(ra, k0 + 2 * kBatch);
+            compute(rb, k0 + kBatch);
         }
 #pragma unroll
         for (int q = 0; q < 2; ++q)
