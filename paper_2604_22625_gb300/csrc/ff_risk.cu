@@ -16,8 +16,8 @@
 // once per window as double-float pairs (exact products of the FP32 inputs,
 // error-free sums in FP32 arithmetic: GB300's FP64 pipe is a small fraction of
 // its FP32 pipe), with Sigma_f in FP64, and risk_ginv_kernel inverts G_j for
-// every first day j in FP64.  risk_stream_kernel streams R once: per stock and
-// row segment, b = sum f_k r_k, s1 = sum r_k, s2 = sum r_k^2 are summed in FP32
+// every first day j in FP64.  risk_stream_kernel streams R once: per stock,
+// b = sum f_k r_k, s1 = sum r_k, s2 = sum r_k^2 are summed in FP32
 // over chunks of kChunk rows and each chunk sum is added into a double-float
 // accumulator (an error-free two-sum), so the FP32 rounding is bounded by the
 // chunk length; risk_finish_kernel applies the stock's inverse and forms the
@@ -237,131 +237,99 @@ __device__ __forceinline__ void fold(float& hi, float& lo, float x) {
 }
 
 // Streaming pass.  A thread holds two adjacent stocks (one 8-byte load per row
-// when n is even, so a warp reads 256 consecutive bytes of a row) and a block
-// kSegs row segments of kStocks = 64 stocks: warp w sums rows
-// [w T / kSegs, (w + 1) T / kSegs), so that many independent loads are in
-// flight per SM.  Per stock and segment: the double-float sums of f_k r_k (P),
-// r_k, r_k^2, the first row with a return and the last row without one; the
-// segments are combined in shared memory (pairs added in segment order) and
-// written to the workspace for risk_finish_kernel.
-constexpr int kLanes = 32;
-constexpr int kStocks = 2 * kLanes;
-constexpr int kSegs = 8;
+// when n is even) and walks every row of the window; the 8 warps of a block
+// hold 512 consecutive stocks and walk the rows together, so each row is read
+// as one contiguous 2 KB span per block (DRAM pages are read whole, not in
+// scattered 256-byte pieces).  Two register buffers of kBatch rows keep the
+// next rows' loads in flight while the current ones are summed.  Per stock:
+// the double-float sums of f_k r_k (P), r_k, r_k^2, the first row with a
+// return and the last row without one, written to the workspace for
+// risk_finish_kernel.
+constexpr int kStocks = 2 * 256;
 
 template <int P, bool kVec>
-__global__ void __launch_bounds__(kLanes * kSegs)
+__global__ void __launch_bounds__(256)
 risk_stream_kernel(const float* __restrict__ F, const float* __restrict__ R, int T, int n,
                    double* __restrict__ sums, int* __restrict__ hist) {
     extern __shared__ float f_s[];   // [T][P] factor returns of this window
     constexpr int NS = P + 2;
-    __shared__ float red_hi[kSegs][NS][kStocks], red_lo[kSegs][NS][kStocks];
-    __shared__ int red_first[kSegs][kStocks], red_lastnan[kSegs][kStocks];
     const int d = blockIdx.y;
     const float* fw = F + (size_t)d * T * P;
     for (int e = threadIdx.x; e < T * P; e += blockDim.x) f_s[e] = fw[e];
     __syncthreads();
-    const int lane = threadIdx.x % kLanes, seg = threadIdx.x / kLanes;
-    const int i0 = blockIdx.x * kStocks + 2 * lane;
-    const int k_lo = (int)((long long)T * seg / kSegs), k_hi = (int)((long long)T * (seg + 1) / kSegs);
+    const int i0 = blockIdx.x * kStocks + 2 * threadIdx.x;
+    if (i0 >= n) return;
     float hi[2][NS], lo[2][NS], ch[2][NS];
 #pragma unroll
     for (int q = 0; q < 2; ++q)
 #pragma unroll
         for (int j = 0; j < NS; ++j) { hi[q][j] = 0.f; lo[q][j] = 0.f; ch[q][j] = 0.f; }
     int first[2] = {1 << 30, 1 << 30}, lastnan[2] = {-1, -1}, inchunk = 0;
-    if (i0 < n) {
-        const bool two = i0 + 1 < n;
-        const float* col = R + (size_t)d * T * n + i0;
-        // rows k0 .. k0 + kBatch - 1 of the stock pair (NaN past the segment)
-        auto load = [&](float2 (&rv)[kBatch], int k0) {
+    const bool two = i0 + 1 < n;
+    const float* col = R + (size_t)d * T * n + i0;
+    // rows k0 .. k0 + kBatch - 1 of the stock pair (NaN past the window)
+    auto load = [&](float2 (&rv)[kBatch], int k0) {
 #pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int k = k0 + u;
-                if (k < k_hi) {
-                    const float* pk = col + (size_t)k * n;
-                    if constexpr (kVec) rv[u] = two ? __ldg((const float2*)pk) : make_float2(__ldg(pk), NAN);
-                    else rv[u] = make_float2(__ldg(pk), two ? __ldg(pk + 1) : NAN);
-                } else {
-                    rv[u] = make_float2(NAN, NAN);
-                }
+        for (int u = 0; u < kBatch; ++u) {
+            const int k = k0 + u;
+            if (k < T) {
+                const float* pk = col + (size_t)k * n;
+                if constexpr (kVec) rv[u] = two ? __ldg((const float2*)pk) : make_float2(__ldg(pk), NAN);
+                else rv[u] = make_float2(__ldg(pk), two ? __ldg(pk + 1) : NAN);
+            } else {
+                rv[u] = make_float2(NAN, NAN);
             }
-        };
-        auto compute = [&](const float2 (&rv)[kBatch], int k0) {
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                const int k = k0 + u;
-                if (k >= k_hi) break;
-                const float* fk = f_s + k * P;
-                float fv[P];
-#pragma unroll
-                for (int j = 0; j < P; ++j) fv[j] = fk[j];
-                const float r2[2] = {rv[u].x, rv[u].y};
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const float r = r2[q];
-                    if (isnan(r)) { lastnan[q] = k; continue; }
-                    first[q] = min(first[q], k);
-#pragma unroll
-                    for (int j = 0; j < P; ++j) ch[q][j] = fmaf(fv[j], r, ch[q][j]);
-                    ch[q][P] += r;
-                    ch[q][P + 1] = fmaf(r, r, ch[q][P + 1]);
-                }
-                // fold every kChunk rows (NaN rows count: a chunk holds at most kChunk terms)
-                if (++inchunk == kChunk) {
-#pragma unroll
-                    for (int q = 0; q < 2; ++q)
-#pragma unroll
-                        for (int j = 0; j < NS; ++j) { fold(hi[q][j], lo[q][j], ch[q][j]); ch[q][j] = 0.f; }
-                    inchunk = 0;
-                }
-            }
-        };
-        // two register buffers: the loads of the next batch are in flight while
-        // the current one is summed
-        float2 ra[kBatch], rb[kBatch];
-        load(ra, k_lo);
-        for (int k0 = k_lo; k0 < k_hi; k0 += 2 * kBatch) {
-            load(rb, k0 + kBatch);
-            compute(ra, k0);
-            load(ra, k0 + 2 * kBatch);
-            compute(rb, k0 + kBatch);
         }
+    };
+    auto compute = [&](const float2 (&rv)[kBatch], int k0) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
+        for (int u = 0; u < kBatch; ++u) {
+            const int k = k0 + u;
+            if (k >= T) break;
+            const float* fk = f_s + k * P;
+            float fv[P];
 #pragma unroll
-            for (int j = 0; j < NS; ++j) fold(hi[q][j], lo[q][j], ch[q][j]);
+            for (int j = 0; j < P; ++j) fv[j] = fk[j];
+            const float r2[2] = {rv[u].x, rv[u].y};
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float r = r2[q];
+                if (isnan(r)) { lastnan[q] = k; continue; }
+                first[q] = min(first[q], k);
+#pragma unroll
+                for (int j = 0; j < P; ++j) ch[q][j] = fmaf(fv[j], r, ch[q][j]);
+                ch[q][P] += r;
+                ch[q][P + 1] = fmaf(r, r, ch[q][P + 1]);
+            }
+            // fold every kChunk rows (NaN rows count: a chunk holds at most kChunk terms)
+            if (++inchunk == kChunk) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+#pragma unroll
+                    for (int j = 0; j < NS; ++j) { fold(hi[q][j], lo[q][j], ch[q][j]); ch[q][j] = 0.f; }
+                inchunk = 0;
+            }
+        }
+    };
+    float2 ra[kBatch], rb[kBatch];
+    load(ra, 0);
+    for (int k0 = 0; k0 < T; k0 += 2 * kBatch) {
+        load(rb, k0 + kBatch);
+        compute(ra, k0);
+        load(ra, k0 + 2 * kBatch);
+        compute(rb, k0 + kBatch);
     }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
+        const int ii = i0 + q;
+        if (q == 1 && !two) break;
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
-            red_hi[seg][j][2 * lane + q] = hi[q][j];
-            red_lo[seg][j][2 * lane + q] = lo[q][j];
+            fold(hi[q][j], lo[q][j], ch[q][j]);
+            sums[((size_t)d * n + ii) * NS + j] = (double)hi[q][j] + (double)lo[q][j];
         }
-        red_first[seg][2 * lane + q] = first[q];
-        red_lastnan[seg][2 * lane + q] = lastnan[q];
-    }
-    __syncthreads();
-    // combine the segments (fixed order) and write: threads (j, stock), j < NS
-    for (int e = threadIdx.x; e < NS * kStocks; e += blockDim.x) {
-        const int j = e / kStocks, l = e % kStocks;
-        const int ii = blockIdx.x * kStocks + l;
-        if (ii >= n) continue;
-        double acc = 0.0;
-        for (int q = 0; q < kSegs; ++q) acc += (double)red_hi[q][j][l] + (double)red_lo[q][j][l];
-        sums[((size_t)d * n + ii) * NS + j] = acc;
-    }
-    if (threadIdx.x < kStocks) {
-        const int ii = blockIdx.x * kStocks + threadIdx.x;
-        if (ii < n) {
-            int f0 = 1 << 30, ln = -1;
-            for (int q = 0; q < kSegs; ++q) {
-                f0 = min(f0, red_first[q][threadIdx.x]);
-                ln = max(ln, red_lastnan[q][threadIdx.x]);
-            }
-            hist[2 * ((size_t)d * n + ii)] = f0;
-            hist[2 * ((size_t)d * n + ii) + 1] = ln;
-        }
+        hist[2 * ((size_t)d * n + ii)] = first[q];
+        hist[2 * ((size_t)d * n + ii) + 1] = lastnan[q];
     }
 }
 
@@ -442,7 +410,7 @@ cudaError_t launch_stream(const float* F, const float* R, int count, int T, int 
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((n + kStocks - 1) / kStocks), (unsigned)count);
-    kern<<<grid, kLanes * kSegs, smem, stream>>>(F, R, T, n, sums, hist);
+    kern<<<grid, 256, smem, stream>>>(F, R, T, n, sums, hist);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     dim3 grid2((unsigned)((n + 127) / 128), (unsigned)count);
