@@ -720,8 +720,11 @@ int ff_solve_joint_batch(const ff_problem* probs, int count, const ff_options* o
     if (o.precision != FF_PREC_F64) return FF_ERR_UNSUPPORTED;
     for (int t = 0; t < count; ++t)
         if (!ff::valid_problem(&probs[t])) return FF_ERR_INVALID_ARG;
-    return ff::joint_solve(probs, count, ff::make_params(o), ws, ws_bytes, result_dev, w_out, yA_out, yD_out,
-                           (cudaStream_t)stream);
+    cudaError_t ce = cudaSuccess;
+    const int rc = ff::joint_solve(probs, count, ff::make_params(o), ws, ws_bytes, result_dev, w_out, yA_out, yD_out,
+                                   (cudaStream_t)stream, &ce);
+    if (rc == FF_ERR_CUDA) ff::cuda_fail(ce, "joint prox solve (instance table copy or kernel launch)");
+    return rc;
 }
 
 size_t ff_workspace_size(const ff_problem* probs, int count, const ff_options* o_in) {

@@ -137,7 +137,7 @@ int choose_tile(int P, int n, int k, int m, int omega_diag, size_t matvec_size, 
 // CTA per instance; FF_ERR_UNSUPPORTED beyond 256 factors or exposure rows.
 size_t joint_workspace_bytes(const ff_problem* probs, int count);
 int joint_solve(const ff_problem* probs, int count, const Params& prm, void* ws, size_t ws_bytes, ff_result* res,
-                void* const* w_out, void* const* yA_out, void* const* yD_out, cudaStream_t st);
+                void* const* w_out, void* const* yA_out, void* const* yD_out, cudaStream_t st, cudaError_t* cuda_err);
 
 // Launch the team kernel over `count` instances (insts is a device array).
 // G = CTAs per instance (cluster size), nteams = concurrent teams; single =

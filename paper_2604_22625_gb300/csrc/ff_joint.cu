@@ -606,7 +606,8 @@ size_t joint_workspace_bytes(const ff_problem* probs, int count) {
 }
 
 int joint_solve(const ff_problem* probs, int count, const Params& prm, void* ws, size_t ws_bytes, ff_result* res,
-                void* const* w_out, void* const* yA_out, void* const* yD_out, cudaStream_t st) {
+                void* const* w_out, void* const* yA_out, void* const* yD_out, cudaStream_t st, cudaError_t* cuda_err) {
+    *cuda_err = cudaSuccess;
     for (int t = 0; t < count; ++t) {
         const ff_problem* p = &probs[t];
         if (p->T != 0) return FF_ERR_UNSUPPORTED;
@@ -644,9 +645,10 @@ int joint_solve(const ff_problem* probs, int count, const Params& prm, void* ws,
         I.ydb = take(n * 8);
     }
     cudaError_t e = cudaMemcpyAsync(base, table.data(), (size_t)count * sizeof(JInst), cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return FF_ERR_CUDA;
+    if (e != cudaSuccess) { *cuda_err = e; return FF_ERR_CUDA; }
     joint_kernel<<<count, kJT, 0, st>>>((const JInst*)base, prm);
-    if (cudaGetLastError() != cudaSuccess) return FF_ERR_CUDA;
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { *cuda_err = e; return FF_ERR_CUDA; }
     return FF_OK;
 }
 
