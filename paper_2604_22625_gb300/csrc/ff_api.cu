@@ -807,7 +807,7 @@ const char* ff_status_string(int code) {
     }
 }
 
-int ff_version(void) { return 200; }   // 0.2.0: ff_grads.wT, multi-period adjoint
+int ff_version(void) { return 300; }   // 0.3.0: ff_options and ff_result fields appended, risk model, joint prox
 
 const char* ff_last_error(void) { return ff::g_last_error; }
 
