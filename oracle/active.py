@@ -21,7 +21,9 @@ The same reduced system gives the implicit-function derivatives used by
 """
 from __future__ import annotations
 
+import time
 from dataclasses import dataclass
+from typing import Optional
 
 import numpy as np
 import scipy.sparse as sp
@@ -257,25 +259,38 @@ def _newton(sc: Scaled, red: Reduced, x0, max_newton: int):
 
 
 def refine(prob, ipm_sol, max_newton: int = 60, rounds: int = 40, accept: float = 1e-12,
-           fallback: float = 1e-9, max_groups: int = 6000):
+           fallback: float = 1e-9, max_groups: int = 6000, seconds: Optional[float] = None):
     """Polish an interior-point solution.  Returns (x, yA, yD, kkt, red) for the
     first activity guess certified to ``accept``, else the best one found if it
-    is certified to ``fallback``, else None."""
+    is certified to ``fallback``, else None.  ``seconds``: wall-clock budget;
+    no new round starts after it (None: rounds only)."""
+    t_start = time.perf_counter()
     sc = Scaled(prob)
     act = ipm_sol.active
-    # kinks of holdings and trades are read from the primal values (reliable to
-    # ~1e-10 at the interior-point exit); rows from the slack/multiplier ratio
+    # kinks: a trade is dead when its interior-point multiplier lies inside the
+    # spread cost's dead zone (|y_D| < c1, Eq. 1 / Eq. 4) or its value is zero
+    # to 1e-9 of the largest trade (the interior point exits near 1e-6 relative
+    # KKT on large multi-period instances, where the primal threshold alone
+    # leaves hundreds of dead trades to be found one Newton step at a time); a
+    # holding is zero to 1e-9 of the largest holding; rows from the
+    # slack/multiplier ratio.  A wrong guess only costs rounds: every result is
+    # accepted only when the independent KKT evaluation certifies it.
     xi = ipm_sol.x
     zi = sc.trades(xi)
     tx = 1e-9 * max(1e-3, float(np.max(np.abs(xi))))
     tz = 1e-9 * max(1e-3, float(np.max(np.abs(zi))))
-    st = dict(zero=np.abs(xi) <= tx, dead=np.abs(zi) <= tz,
+    dead = np.abs(zi) <= tz
+    if getattr(ipm_sol, "yD", None) is not None:
+        dead |= np.abs(np.asarray(ipm_sol.yD).reshape(zi.shape)) < sc.c1 * (1.0 - 1e-4)
+    st = dict(zero=np.abs(xi) <= tx, dead=dead,
               budget=np.asarray(act["budget"]).copy(), upper=act["upper"].copy(),
               lower=act["lower"].copy(), sx_force=np.zeros((sc.P, sc.n)),
               sz_force=np.zeros((sc.R, sc.n)))
     x = ipm_sol.x.copy()
     best = None
     for _ in range(rounds):
+        if seconds is not None and time.perf_counter() - t_start > seconds:
+            break
         red = _identify(sc, x, st)
         if red.S.shape[1] > max_groups:
             return None

@@ -30,12 +30,16 @@ class OracleSolution:
         return self.x[0] if self.x.shape[0] == 1 else self.x
 
 
-def solve(prob, polish: bool = True, polish_max_vars: int = 120000) -> OracleSolution:
-    """FP64 minimiser of the scaled model of ``prob`` (single or multi-period)."""
+def solve(prob, polish: bool = True, polish_max_vars: int = 120000,
+          polish_seconds: float = 60.0) -> OracleSolution:
+    """FP64 minimiser of the scaled model of ``prob`` (single or multi-period).
+    The active-set polish gets ``polish_seconds`` of wall clock; when it does
+    not certify a point in that time the interior-point point is returned
+    (``polished`` False), with its own KKT evaluation."""
     sc = Scaled(prob)
     sol = ipm.solve(prob)
     if polish and sc.P * sc.n <= polish_max_vars:
-        ref = active.refine(prob, sol)
+        ref = active.refine(prob, sol, seconds=polish_seconds)
         if ref is not None:
             x, yA, yD, res, red = ref
             return OracleSolution(x, yA, yD, sc.objective(x), sc.paper_objective(x), res, True,
