@@ -238,3 +238,15 @@ def test_paper_objective_units():
     direct = (p.GMV * p.alpha @ w - p.lam1 * p.GMV ** 2 * w @ Sigma @ w
               - p.lam2 * p.GMV * p.s @ tr - p.lam3 * p.GMV * p.q @ tr ** p.d)
     assert abs(direct - sol.paper_obj) <= 1e-9 * abs(direct)
+
+
+def test_polish_budget_and_certificate():
+    """The polish either certifies its point (relative KKT <= 1e-12 by the
+    independent evaluation) or the interior-point point comes back unpolished;
+    with no time budget left no polish round starts."""
+    prob = S.make_multi(4, 60, 3, 71, n_onehot=1)
+    full = oracle.solve(prob)
+    assert full.polished and full.kkt.rel_kkt <= 1e-12
+    none = oracle.solve(prob, polish_seconds=0.0)
+    assert not none.polished
+    assert float(np.max(np.abs(none.x - full.x))) <= 1e-5
