@@ -10,9 +10,19 @@ instances (n ~ U{500..8000}, k in {40, 80}) and 64 multi-period instances
 (T ~ U{5..40}, n ~ U{1000..4000}), BF16 F and A panels, FP32 matvecs, FP64
 iterate state and FP64 KKT reductions, solved by one call of ff_solve_batch.
 One step = one call: the batched repack of all inputs into the solver layout
-(one launch) and the persistent solver launch over all 576 instances.
+(one launch) and the persistent solver launches over all 576 instances (one
+per cluster-size group, concurrent), plus the FP64 re-solve of instances that
+stop at the FP32 rounding floor.  The batch runs at cta_work 16384 and
+check_every 128, the fastest point of the autotuner's grid for this batch
+(--cta-work / --check-every, or --tuned to run the autotuner).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Other workloads (--workload): diff (forward and batched adjoint), risk (the
+risk model of Sec. 3.2 over 21 windows), joint (the joint primal prox
+variant against the plain split), paper_grid (the lambda grid of Sec. 4.1 on
+paper-shaped synthetic instances), single_small, single_large, multi (one
+instance each).
 
 Under torchrun (N > 1) every rank solves its own batch (seeded by rank) with
 no collective on the data path: weak scaling; rank 0 prints one JSON line.
