@@ -234,7 +234,8 @@ size_t ff_joint_workspace_size(const ff_problem* probs, int count);
  * the KKT test's trade multiplier is the cost's slope phi'(w - w0), or on the
  * cost's kink (w = w0) the remainder of the prox's optimality condition.
  * FP64 throughout, one CTA per instance; o->precision must be FF_PREC_F64
- * (else FF_ERR_UNSUPPORTED), every instance single-period (T = 0) with k <= 256
+ * (else FF_ERR_UNSUPPORTED; o = NULL gives the defaults with FF_PREC_F64),
+ * every instance single-period (T = 0) with k <= 256
  * and m <= 256 (else FF_ERR_UNSUPPORTED).  warm_start, cluster_size, cta_work,
  * max_teams, stall_checks, round_panels_bf16, panel_l2_keep, primal_weight and
  * the test hook have no effect.  Arguments and outputs as ff_solve_batch

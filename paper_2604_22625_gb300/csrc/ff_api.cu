@@ -715,7 +715,12 @@ int ff_solve_joint_batch(const ff_problem* probs, int count, const ff_options* o
                          void* stream) {
     if (!probs || count < 1 || count > 65535 || !result_dev || !w_out) return FF_ERR_INVALID_ARG;
     ff_options o;
-    if (o_in) o = *o_in; else ff::fill_defaults(&o);
+    if (o_in) {
+        o = *o_in;
+    } else {
+        ff::fill_defaults(&o);
+        o.precision = FF_PREC_F64;   // the variant's only precision
+    }
     if (!ff::valid_options(o)) return FF_ERR_INVALID_ARG;
     if (o.precision != FF_PREC_F64) return FF_ERR_UNSUPPORTED;
     for (int t = 0; t < count; ++t)

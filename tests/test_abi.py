@@ -218,3 +218,7 @@ def test_joint_host_checks(lib):
     assert _lib.ff_solve_joint_batch(one, 1, o64, 4096, ws1 - 256, 4096, [4096]) == _lib.FF_ERR_WORKSPACE
     assert _lib.ff_solve_joint_batch(one, 1, o64, 4096 + 8, ws1, 4096, [4096]) == _lib.FF_ERR_WORKSPACE
     assert _lib.ff_solve_joint_batch(one, 1, o64, 4096, ws1, 4096, [None]) == _lib.FF_ERR_INVALID_ARG
+    # no options: the defaults in FP64, so only the short workspace is refused
+    rc = _lib.load().ff_solve_joint_batch(one, 1, None, C.c_void_p(4096), ws1 - 256, C.c_void_p(4096),
+                                          (C.c_void_p * 1)(4096), None, None, None)
+    assert rc == _lib.FF_ERR_WORKSPACE
